@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Throughput of the SCSC code update (Eq. 3 by proximal gradient with
+randomized code-coordinate subsampling) on GB300.
+
+One step = one scsc_code_step call over one batch: draw M^t, pack the warm
+start on the sampled set, the step-size power iteration, n_iters proximal-
+gradient iterations (masked synthesis, residual, adjoint at the sampled
+coordinates, soft threshold), up-projection to dense codes (Eq. 4).
+Metric: Gpix.filter/s = sum_n H_n W_n * K * n_iters / step time.
+
+Default workload: 64 images 256x256 of the blob generator, K = 100 filters
+11x11, p = 1/4, lambda = 1, 100 iterations per step, BF16 tensor path.
+Multi-GPU: each rank processes its own batch (different image ids), no
+collective on the data path; value = all ranks' work / max time.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (H list builder, K, p, n_iters)
+    "c3": dict(n=64, H=256, W=256, K=100, p=(1, 4), n_iters=100,
+               desc="64 x 256x256 blob images, K=100 11x11, p=1/4, lambda=1, 100 PG its/step"),
+    "c1": dict(n=1, H=100, W=100, K=16, p=(1, 2), n_iters=20,
+               desc="1 x 100x100 blob image, K=16 11x11, p=1/2, lambda=1, 20 PG its/step"),
+    "c5": dict(n=512, H=None, W=None, K=100, p=(1, 4), n_iters=20,
+               desc="512 blob images, H,W uniform in {64..512}, K=100 11x11, p=1/4, 20 PG its/step"),
+}
+
+
+def make_inputs(wl, rank):
+    from paper_1909_00145_gb300 import inputs as I
+    if wl["H"] is None:
+        H, W = I.uneven_sizes(1000 + rank, wl["n"])
+    else:
+        H = np.full(wl["n"], wl["H"], dtype=np.int32)
+        W = np.full(wl["n"], wl["W"], dtype=np.int32)
+    ids = np.arange(wl["n"], dtype=np.int64) + rank * wl["n"]
+    x = I.images(10 + rank, H, W)
+    d = I.filters(7, wl["K"], 11)
+    return H, W, ids, x, d
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), float(p.get("bf16_tflops_sustained",
+                                                                        p["bf16_tflops"])), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def launches_per_step(path: str, n_iters: int) -> int:
+    """Kernels the library launches in one scsc_code_step (counted from the
+    host orchestration): mask 1; power iteration 3 + 50 * 4 + 4; then
+    plain: apply-mask 1 + 2 per iteration;
+    tensor: filter images 1, segment counts 1, scan 3, pack 1, 3 per iteration, unpack 1."""
+    base = 1 + (3 + 50 * 4 + 4)
+    if path == "fp32":
+        return base + 1 + 2 * n_iters
+    return base + 1 + 1 + 3 + 1 + 3 * n_iters + 1
+
+
+def cpu_baseline(wl, budget_s=20.0):
+    """Time the FP64 oracle's proximal-gradient iterations on one image of the
+    workload on the host cores (bounded sample)."""
+    from oracle import reference as R
+    H, W, ids, x, d = make_inputs(dict(wl, n=1), 0)
+    cfg = R.Config(K=wl["K"], s=11, lam=1.0, p_num=wl["p"][0], p_den=wl["p"][1], seed=0)
+    b = R.Batch(H=H[:1], W=W[:1], ids=ids[:1])
+    z = np.zeros(int(H[0]) * int(W[0]) * wl["K"])
+    step = 1.0 / 200.0  # fixed step: the sample times the PG iterations only
+    t0 = time.perf_counter()
+    R.code_step(cfg, b, x, d, z, 1, 1, step=step)
+    one = time.perf_counter() - t0
+    iters = max(1, int(budget_s / max(one, 1e-3)))
+    t0 = time.perf_counter()
+    R.code_step(cfg, b, x, d, z, 1, iters, step=step)
+    el = time.perf_counter() - t0
+    pf = int(H[0]) * int(W[0]) * wl["K"] * iters
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": pf / el / 1e9, "unit": "Gpix*filter/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 image {int(H[0])}x{int(W[0])} of the workload, K={wl['K']}, "
+                      f"{iters} PG iterations (FP64, dense adjoint, OpenMP), {el:.1f} s"}
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import reference as R
+    H, W, ids, x, d = make_inputs(dict(wl, n=1), 0)
+    cfg = R.Config(K=wl["K"], s=11, lam=1.0, p_num=wl["p"][0], p_den=wl["p"][1], seed=0)
+    b = R.Batch(H=H[:1], W=W[:1], ids=ids[:1])
+    z = np.zeros(int(H[0]) * int(W[0]) * wl["K"])
+    step = 1.0 / 200.0
+    t0 = time.perf_counter()
+    R.code_step(cfg, b, x, d, z, 1, 1, step=step)
+    one = time.perf_counter() - t0
+    per_step = max(1, int(4.0 / max(one, 1e-3)))
+    for i in range(args.warmup):
+        z = R.code_step(cfg, b, x, d, z, 1, per_step, step=step)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        z = R.code_step(cfg, b, x, d, z, 1, per_step, step=step)
+    el = time.perf_counter() - t0
+    pf = int(H[0]) * int(W[0]) * wl["K"] * per_step * args.steps
+    val = pf / el / 1e9
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    out = {"impl": "reference", "metric": "code-update Gpix*filter/s", "value": val,
+           "unit": "Gpix*filter/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": wl["desc"]},
+           "cpu_baseline": {"value": val, "unit": "Gpix*filter/s", "cores": cores, "kind": "oracle",
+                            "sample": f"1 image {int(H[0])}x{int(W[0])}, {per_step} PG its per step"},
+           "e2e": {"value": val, "unit": "Gpix*filter/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1909_00145_gb300 import scsc
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    H, W, ids, x_np, d_np = make_inputs(wl, rank)
+    K, n_iters = wl["K"], wl["n_iters"]
+    batch = scsc.Batch(H, W, ids)
+    npx = batch.total_pixels
+    stream = torch.cuda.Stream()
+    x = torch.from_numpy(x_np).cuda()
+    d = torch.from_numpy(d_np).cuda().contiguous()
+    z = torch.zeros(npx * K, dtype=torch.float32, device="cuda")
+    ctx = scsc.Context(K, 11, 1.0, wl["p"], seed=0, prec=args.prec, stream=stream)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            ctx.code_step(batch, x, d, z, 1 + i, n_iters)
+        ctx.sync()
+        scsc.scsc_diag_profile(ctx, True)
+        sampler = ClockSampler(local)
+        barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(args.steps):
+            ctx.code_step(batch, x, d, z, 100 + i, n_iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ctx.sync()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    per_step_ms = ms / args.steps
+    units = npx * K * n_iters * args.steps * world
+    value = units / (ms / 1e3) / 1e9
+
+    # dominant kernel and its roofline
+    kt = {}
+    for name in ["synth_tc", "adj_tc", "finalize_r", "synth_fp32", "adjoint_fp32", "pack",
+                 "unpack", "power", "mask"]:
+        tot, n = scsc.scsc_diag_kernel_time(ctx, name)
+        if n:
+            kt[name] = (tot, n)
+    scsc.scsc_diag_profile(ctx, False)
+    dom = max(kt, key=lambda k: kt[k][0]) if kt else None
+    hbm, bf16, bf16s, src = peaks()
+    sampled = float(wl["p"][0]) / wl["p"][1] * npx * K  # expected sampled coordinates
+    kw = (K + 31) // 32
+    roof = None
+    if dom is not None:
+        avg_s = kt[dom][0] / kt[dom][1] / 1e3
+        # algorithmic bytes per launch (stated per kernel in the design notes)
+        bytes_per_launch = {
+            "adj_tc": 8 * sampled + 4 * kw * npx + 4 * npx,       # packed r+w, mask, residual
+            "synth_tc": 4 * sampled + 4 * kw * npx + 4 * npx,     # packed read, mask, xhat write
+            "adjoint_fp32": 8 * sampled + 4 * kw * npx + 4 * npx,
+            "synth_fp32": 4 * npx * K + 8 * npx,
+        }.get(dom)
+        if bytes_per_launch is not None:
+            ach = bytes_per_launch / avg_s / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm, "traffic": None, "peak_source": src,
+                    "avg_launch_ms": avg_s * 1e3}
+
+    # end to end through the public API with host buffers
+    xh = torch.from_numpy(x_np).pin_memory()
+    dh = torch.from_numpy(d_np).contiguous().pin_memory()
+    zh = torch.zeros(npx * K, dtype=torch.float32).pin_memory()
+    with torch.cuda.stream(stream):
+        xd, dd, zd = torch.empty_like(x), torch.empty_like(d), torch.empty_like(z)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            xd.copy_(xh, non_blocking=True)
+            dd.copy_(dh, non_blocking=True)
+            zd.copy_(zh, non_blocking=True)
+            ctx.code_step(batch, xd, dd, zd, 200 + i, n_iters)
+            zh.copy_(zd, non_blocking=True)
+            stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = npx * K * n_iters * args.e2e_steps * world / e2e_s / 1e9
+    h2d = x.numel() * 4 + d.numel() * 4 + z.numel() * 4
+    d2h = z.numel() * 4
+
+    if rank == 0:
+        out = {"metric": "code-update Gpix*filter/s", "value": value, "unit": "Gpix*filter/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+               "config": {"workload": wl["desc"], "images_per_gpu": int(len(H)),
+                          "pixels_per_gpu": npx, "K": K, "p": f"{wl['p'][0]}/{wl['p'][1]}",
+                          "n_iters": n_iters, "path": args.prec,
+                          "l2": "inputs larger than L2 (dense codes %.2f GB)" % (npx * K * 4 / 1e9)},
+               "clocks": clocks,
+               "roofline": roof,
+               "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+               "e2e": {"value": e2e_val, "unit": "Gpix*filter/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h},
+               "gpu_launches": launches_per_step(args.prec, n_iters) * args.steps}
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(wl)
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * scsc.h -- C ABI of the GB300 library for stochastic convolutional sparse
+ * coding (Xiong, Richtarik & Heidrich, "Stochastic Convolutional Sparse
+ * Coding", 2019).
+ *
+ * Problem (Eq. 1): for every image x_n of H_n x W_n pixels,
+ *     min_{d,z} 1/2 ||x_n - sum_k d_k * z_{n,k}||^2 + lambda sum_k ||z_{n,k}||_1
+ *     s.t. ||d_k||_2 <= 1,
+ * with K filters d_k of s x s taps (s odd, centre c = (s-1)/2) and codes z_k
+ * of the image's size.  Convolution is the true (flipped) convolution with
+ * zero padding:  (d_k * z_k)(i,j) = sum_{u,v} d_k(u,v) z_k(i+c-u, j+c-v).
+ *
+ * Memory conventions (all device pointers unless stated otherwise):
+ *   x : float32 images packed back to back; image n starts at pixel
+ *       offsets[n], row-major H[n] x W[n].
+ *   z : float32 codes, image n starts at offsets[n] * K, layout [H][W][K]
+ *       (filter index innermost).
+ *   d : float32 filters [K][s][s].
+ * The caller owns x, z and d; the library owns every workspace it needs and
+ * grows it on demand.  Calls are asynchronous on the context's stream except
+ * where a host-side result is returned (scsc_objective, scsc_lipschitz_codes,
+ * scsc_online_save); those synchronise the stream.  A context is not
+ * thread-safe.  Errors are returned as scsc_status codes; argument errors are
+ * found on the host before anything is launched, and scsc_last_error() holds
+ * a one-line description.  Device code never traps.
+ */
+#ifndef SCSC_H
+#define SCSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SCSC_OK = 0,
+  SCSC_EINVAL = 1,       /* bad argument (detected on the host)            */
+  SCSC_ENOMEM = 2,       /* device or pinned-host allocation failed        */
+  SCSC_ECUDA = 3,        /* a CUDA runtime call or a kernel launch failed  */
+  SCSC_ETIMEOUT = 4,     /* a bounded device-side wait ran out             */
+  SCSC_ENONFINITE = 5,   /* NaN/Inf found in an input                      */
+  SCSC_EUNSUPPORTED = 6  /* valid request that this build does not support */
+} scsc_status;
+
+typedef enum {
+  SCSC_FP32 = 0, /* plain path: FP32 SIMT kernels on dense FP32 codes          */
+  SCSC_BF16 = 1  /* tensor path: BF16 operands on tcgen05, FP32 accumulation,
+                    FP32 master codes, FP32 residual / prox / projection        */
+} scsc_precision;
+
+typedef enum {
+  SCSC_DICT_BATCH = 0, /* Eq. 5, one projected-gradient step (Alg. 1 line 8)   */
+  SCSC_DICT_ONLINE = 1 /* Eq. 7 surrogate update + one projected-gradient step
+                          on Eq. 8 (Alg. 2 lines 8-9)                          */
+} scsc_dict_mode;
+
+typedef struct {
+  int K;             /* number of filters, 1 <= K <= 512                        */
+  int s;             /* filter side, odd, 1 <= s <= 11                          */
+  double lambda;     /* L1 weight of Eq. 1 (> 0)                               */
+  uint32_t p_num;    /* subsampling rate p = p_num / p_den, 0 <= p <= 1         */
+  uint32_t p_den;    /* (Sec. 3.1: Bernoulli(p) per code coordinate)           */
+  uint64_t seed;     /* seed of the counter-based subsampling hash             */
+  scsc_precision prec;
+  double step;       /* > 0: fixed code step alpha; 0: alpha = 1 / L_z          */
+} scsc_config;
+
+typedef struct {   /* host arrays, n_images entries each */
+  int n_images;
+  const int64_t *offsets;   /* pixel offset of each image in x            */
+  const int *H;             /* rows    (>= 1)                             */
+  const int *W;             /* columns (>= 1)                             */
+  const int64_t *image_ids; /* global image index n used by the hash      */
+} scsc_batch;
+
+typedef struct scsc_ctx scsc_ctx;
+
+/* Create a context bound to the current CUDA device and `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Validates cfg. */
+scsc_status scsc_create(const scsc_config *cfg, void *cuda_stream, scsc_ctx **out);
+
+/* Free the context and every workspace it owns.  NULL is accepted. */
+scsc_status scsc_destroy(scsc_ctx *ctx);
+
+/* One-line description of the last error on this context ("" if none). */
+const char *scsc_last_error(const scsc_ctx *ctx);
+
+/* Subsampling matrix M^t of outer iteration t (Sec. 3.1) as a bitmask:
+ * bits_dev is uint32 [total_pixels][ceil(K/32)], bit (k % 32) of word k / 32
+ * of pixel q is set when code coordinate (q, k) is sampled.  Coordinate
+ * (k, y, x) of image n is sampled iff hi32(h) < floor(p * 2^32) with
+ * h = mix(mix(mix(mix(seed) ^ t) ^ n) ^ ((k*H + y)*W + x)) and mix the
+ * SplitMix64 output function. */
+scsc_status scsc_mask(scsc_ctx *ctx, const scsc_batch *batch, uint64_t t, uint32_t *bits_dev);
+
+/* One outer iteration of the code update (Alg. 1 lines 4-7, Alg. 2 lines
+ * 5-7): draw M^t, take the previous codes on the sampled coordinates as the
+ * warm start, run n_iters proximal-gradient steps on Eq. 3
+ *     r = D z - x;   z_S <- soft(z_S - alpha (D^T r)_S, alpha lambda),
+ * and write the Eq. 4 codes (zero off the sampled set) back to z_dev.
+ * alpha = cfg.step if > 0, else 1 / L_z with L_z = 1.01 x the 50-step power
+ * iteration estimate of lambda_max(D D^T) on the batch's max(H) x max(W)
+ * domain.  n_iters >= 0; n_iters = 0 only applies Eq. 4 to the warm start. */
+scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                           const float *d_dev, float *z_dev, uint64_t t, int n_iters);
+
+/* Dictionary update.  SCSC_DICT_BATCH (Eq. 5): r = D z - x,
+ * G_k(u,v) = sum_n sum_{i,j} r(i,j) z_k(i+c-u, j+c-v),
+ * d_k <- P(d_k - G_k / L_d) with L_d from the power-iteration rule on
+ * sum_n Z_n^T Z_n and P the projection onto ||d_k|| <= 1.
+ * SCSC_DICT_ONLINE (Eq. 7-8, t >= 1 counts mini-batches): C, B <- (t-1)/t
+ * C, B + (1/t) mean_n Z_n^T Z_n, Z_n^T x_n; d <- P(d - (C d - B) / L_C). */
+scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                           const float *z_dev, float *d_dev, scsc_dict_mode mode, uint64_t t);
+
+/* Eq. 1 summed over the batch, accumulated in FP64; synchronises. */
+scsc_status scsc_objective(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                           const float *z_dev, const float *d_dev, double *out_host);
+
+/* L_z = 1.01 x power-iteration estimate of lambda_max(D D^T) on the batch's
+ * max(H) x max(W) domain (the step-size rule of scsc_code_step); synchronises. */
+scsc_status scsc_lipschitz_codes(scsc_ctx *ctx, const scsc_batch *batch, const float *d_dev,
+                                 double *out_host);
+
+/* Synthesis xhat = sum_k d_k * (m_k . z_k) (Sec. 3.1, D (M^t)^T z~): masked
+ * = 1 applies M^t of iteration t, masked = 0 uses every coordinate.
+ * xhat_dev is float32 packed like x. */
+scsc_status scsc_synth(scsc_ctx *ctx, const scsc_batch *batch, const float *z_dev,
+                       const float *d_dev, uint64_t t, int masked, float *xhat_dev);
+
+/* Backward of scsc_synth for an upstream gradient g (packed like x):
+ * grad_z = m . (D^T g)  (layout of z), grad_d_k(u,v) = sum g(i,j) (m.z)_k(i+c-u, j+c-v).
+ * Either output may be NULL.  Outputs are overwritten, not accumulated. */
+scsc_status scsc_synth_backward(scsc_ctx *ctx, const scsc_batch *batch, const float *grad_dev,
+                                const float *z_dev, const float *d_dev, uint64_t t, int masked,
+                                float *grad_z_dev, float *grad_d_dev);
+
+/* Wait for all work queued on the context, then report a device-side error
+ * recorded by the tensor-core kernels: SCSC_ETIMEOUT when one of their
+ * bounded waits on an mbarrier ran out (the kernel then skipped its
+ * remaining work and released its tensor memory). */
+scsc_status scsc_sync(scsc_ctx *ctx);
+
+/* Online surrogates (Eq. 7): reset to C = 0, B = 0, t = 0; query the byte
+ * size of the serialised state; save to / load from a host buffer
+ * (format: magic, K, s, t, then C [KM][KM] float32 and B [KM] float64). */
+scsc_status scsc_online_reset(scsc_ctx *ctx);
+scsc_status scsc_online_state_size(scsc_ctx *ctx, size_t *bytes);
+scsc_status scsc_online_save(scsc_ctx *ctx, void *host_buf, size_t bytes);
+scsc_status scsc_online_load(scsc_ctx *ctx, const void *host_buf, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCSC_H */

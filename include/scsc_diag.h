@@ -1,0 +1,41 @@
+/*
+ * scsc_diag.h -- diagnostic entry points of the SCSC library.
+ *
+ * scsc_diag_tc_gemm runs one tcgen05 matrix multiply through the same
+ * shared-memory descriptor, instruction descriptor and TMEM read-back code
+ * that the tensor-core code update uses, so that their encodings can be
+ * checked on the device against a plain product:
+ *     D[128 x N] = A[128 x 64] * B[N x 64]^T,
+ * A, B float32 row-major device arrays whose values are rounded to BF16,
+ * D float32 row-major [128][N] device array, N a multiple of 16 in [16, 256].
+ * Runs on the legacy default stream and synchronises the device.  Returns
+ * SCSC_OK, SCSC_ENOMEM if its one-word error flag cannot be allocated,
+ * SCSC_ECUDA on an invalid N or a launch error, SCSC_ETIMEOUT if the MMA's
+ * completion barrier was not reached within one second.  The paper has no
+ * counterpart: this checks the build's instruction encodings.
+ */
+#ifndef SCSC_DIAG_H
+#define SCSC_DIAG_H
+#include "scsc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+scsc_status scsc_diag_tc_gemm(int N, const float *A_dev, const float *B_dev, float *D_dev);
+
+/* Per-kernel timing.  scsc_diag_profile(ctx, 1) synchronises the context's
+ * stream, clears the records and from then on brackets every launch of the
+ * library's kernels with a pair of CUDA events on that stream; 0 turns it
+ * off.  scsc_diag_kernel_time() waits for the recorded events and returns the
+ * summed device time and the launch count of one kernel, named "mask",
+ * "power", "synth_fp32", "adjoint_fp32", "pack", "synth_tc", "finalize_r",
+ * "adj_tc" or "unpack" (SCSC_EINVAL for another name). */
+scsc_status scsc_diag_profile(scsc_ctx *ctx, int enable);
+scsc_status scsc_diag_kernel_time(scsc_ctx *ctx, const char *name, double *total_ms,
+                                  int *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

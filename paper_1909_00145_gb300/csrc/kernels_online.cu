@@ -1,0 +1,176 @@
+// kernels_online.cu -- online surrogates of Eq. 7 and the matrix-vector
+// products of Eq. 8, plus small helpers.
+//
+// Z_n is the code Toeplitz matrix of image n: row (i,j), column (k,u,v),
+// entry z_k(i+c-u, j+c-v).  The surrogate update
+//     C <- a C + b sum_n Z_n^T Z_n,     B <- a B + b sum_n Z_n^T x_n
+// is an implicit GEMM over all pixels of the batch: Z is never materialised,
+// its entries are gathered from the codes while staging tiles in shared memory.
+#include "scsc_internal.cuh"
+
+namespace scsc {
+
+namespace {
+
+constexpr int kTB = 64;   // C tile edge
+constexpr int kPB = 16;   // pixels per staged chunk
+
+// Entry (row = pixel q of the batch, column col = (k,u,v)) of Z.
+__device__ __forceinline__ float z_entry(const BatchDev &b, int K, int S, const float *z, int n,
+                                         int y, int x, int col) {
+  const int M = S * S, C = (S - 1) / 2;
+  int k = col / M, m = col - k * M, u = m / S, v = m - u * S;
+  int yy = y + C - u, xx = x + C - v;
+  int H = b.H[n], W = b.W[n];
+  if (yy < 0 || yy >= H || xx < 0 || xx >= W) return 0.0f;
+  return z[(b.off[n] + (int64_t)yy * W + xx) * K + k];
+}
+
+// C[a][b] = alpha C[a][b] + beta sum_q Z[q][a] Z[q][b] for a 64x64 tile;
+// 256 threads, 4x4 outputs each, FP32 accumulation per tile pass.
+__global__ void __launch_bounds__(256) surrogate_gemm_kernel(BatchDev b, int K, int S,
+                                                             const float *__restrict__ z,
+                                                             int KM, float alpha, float beta,
+                                                             float *__restrict__ Cm) {
+  __shared__ float As[kPB][kTB + 4];
+  __shared__ float Bs[kPB][kTB + 4];
+  const int a0 = blockIdx.y * kTB, b0 = blockIdx.x * kTB;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4] = {};
+  for (int64_t q0 = 0; q0 < b.total_px; q0 += kPB) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPB * kTB; i += blockDim.x) {
+      int p = i / kTB, c = i - p * kTB;
+      int64_t q = q0 + p;
+      float va = 0.0f, vb = 0.0f;
+      if (q < b.total_px) {
+        int n = upper_index(b.off, b.n, q);
+        int64_t local = q - b.off[n];
+        int W = b.W[n];
+        int y = (int)(local / W), x = (int)(local - (int64_t)y * W);
+        if (a0 + c < KM) va = z_entry(b, K, S, z, n, y, x, a0 + c);
+        if (b0 + c < KM) vb = z_entry(b, K, S, z, n, y, x, b0 + c);
+      }
+      As[p][c] = va;
+      Bs[p][c] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < kPB; ++p) {
+      float ra[4], rb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        ra[i] = As[p][ty * 4 + i];
+        rb[i] = Bs[p][tx * 4 + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(ra[i], rb[j], acc[i][j]);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int a = a0 + ty * 4 + i, c = b0 + tx * 4 + j;
+      if (a < KM && c < KM) {
+        float *p = Cm + (int64_t)a * KM + c;
+        *p = alpha * *p + beta * acc[i][j];
+      }
+    }
+}
+
+// B[col] = alpha B[col] + beta sum_q Z[q][col] x[q]  (FP64 accumulation)
+__global__ void surrogate_b_kernel(BatchDev b, int K, int S, const float *__restrict__ z,
+                                   const float *__restrict__ x, int KM, double alpha, double beta,
+                                   double *__restrict__ Bv) {
+  const int col = blockIdx.x;
+  double s = 0.0;
+  for (int64_t q = threadIdx.x; q < b.total_px; q += blockDim.x) {
+    int n = upper_index(b.off, b.n, q);
+    int64_t local = q - b.off[n];
+    int W = b.W[n];
+    int y = (int)(local / W), xcol = (int)(local - (int64_t)y * W);
+    float e = z_entry(b, K, S, z, n, y, xcol, col);
+    if (e != 0.0f) s += (double)e * (double)x[q];
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) Bv[col] = alpha * Bv[col] + beta * red[0];
+}
+
+// out[a] = sum_b C[a][b] v[b] (- Bv[a]), one warp per row, FP64 accumulation.
+template <bool kGrad>
+__global__ void symv_kernel(const float *__restrict__ Cm, int64_t n, const float *__restrict__ v,
+                            const double *__restrict__ Bv, float *__restrict__ outf,
+                            double *__restrict__ outd) {
+  int64_t row = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
+  int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const float *cr = Cm + row * n;
+  double s = 0.0;
+  for (int64_t j = lane; j < n; j += 32) s += (double)cr[j] * (double)v[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    if (kGrad) outd[row] = s - Bv[row];
+    else outf[row] = (float)s;
+  }
+}
+
+__global__ void double_to_float_kernel(const double *in, float *out, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
+__global__ void set_step_kernel(StepParams *prm, double step, double lambda) {
+  prm->alpha = (float)step;
+  prm->thresh = (float)(step * lambda);
+}
+
+}  // namespace
+
+cudaError_t launch_surrogate_update(const BatchDev &b, int K, int s, const float *z, const float *x,
+                                    double alpha, double beta, float *Cm, double *Bv,
+                                    cudaStream_t st) {
+  const int KM = K * s * s;
+  dim3 grid((KM + kTB - 1) / kTB, (KM + kTB - 1) / kTB);
+  surrogate_gemm_kernel<<<grid, 256, 0, st>>>(b, K, s, z, KM, (float)alpha, (float)beta, Cm);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  surrogate_b_kernel<<<KM, 256, 0, st>>>(b, K, s, z, x, KM, alpha, beta, Bv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symv(const float *Cm, int64_t n, const float *v, const double *unused, float *out,
+                        cudaStream_t st) {
+  (void)unused;
+  int64_t blocks = (n + 7) / 8;
+  symv_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(Cm, n, v, nullptr, out, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symv_grad(const float *Cm, int64_t n, const float *d, const double *Bv,
+                             double *out, cudaStream_t st) {
+  int64_t blocks = (n + 7) / 8;
+  symv_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(Cm, n, d, Bv, nullptr, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_double_to_float(const double *in, float *out, int n, cudaStream_t st) {
+  double_to_float_kernel<<<(n + 255) / 256, 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_step(StepParams *prm, double step, double lambda, cudaStream_t st) {
+  set_step_kernel<<<1, 1, 0, st>>>(prm, step, lambda);
+  return cudaGetLastError();
+}
+
+}  // namespace scsc

@@ -1,0 +1,833 @@
+// kernels_tc.cu -- tensor-core code update (Eq. 3 by proximal gradient) on
+// sm_103a: BF16 operands in shared memory, FP32 accumulators in TMEM.
+//
+// Work unit ("row item"): one image row a of one 128-column strip js of
+// image n, i.e. 128 code pixels = the M = 128 rows of one tcgen05 MMA.
+// Items are ordered (n, js, a); a persistent CTA takes a contiguous range.
+//
+// Sampled codes (the pDK variables of Eq. 3) are stored packed in FP32,
+// chunk-major per item: for each 16-filter chunk c of item q, the sampled
+// values of its 128 pixels in pixel order, each pixel's in filter order,
+// starting at seg_base[q * NC + c].  Unsampled codes are not stored (Eq. 4).
+//
+// Synthesis  P[p][(u,v)] = sum_k z_k(a, b0+p) d_k(u,v)  (MMA, N = 16 s taps)
+//            xhat(a-c+u, b0+p-c+v) += P[p][(u,v)]       (col2im, registers)
+// Adjoint    G[p][k] = sum_u sum_v r(a-c+u, b0+p-c+v) d_k(u,v)
+//            one MMA per tap row u: the A operand is a Toeplitz view of the
+//            residual row a-c+u (8 shifted copies, LBO = SBO = 128 bytes).
+// Prox       z <- soft(z - alpha G, alpha lambda) on the packed values.
+#include <algorithm>
+#include <cstring>
+
+#include "scsc_internal.cuh"
+#include "scsc_tc.cuh"
+#include "tc_ptx.cuh"
+
+namespace scsc {
+namespace {
+
+constexpr int kStrip = 128;
+constexpr int kThreads = 128;
+constexpr uint64_t kWaitNs = 1000000000ull;  // bounded waits: 1 s
+constexpr int kPad = 10;                     // col2im padding (>= 2c)
+constexpr int kPuRow = kStrip + 2 * kPad;    // 148
+
+struct ItemMap {
+  int n;
+  const int *item0;  // [n + 1]
+  const int *H;
+  const int *W;
+  const int64_t *off;
+  int total;
+};
+
+struct Item {
+  int n, js, a, H, W, JS;
+  int64_t base;
+  int q_row0;  // item index of row 0 of this strip
+};
+
+__device__ __forceinline__ Item item_of(const ItemMap &m, int q) {
+  Item it;
+  it.n = upper_index(m.item0, m.n, q);
+  it.H = m.H[it.n];
+  it.W = m.W[it.n];
+  it.JS = (it.W + kStrip - 1) / kStrip;
+  int local = q - m.item0[it.n];
+  it.js = local / it.H;
+  it.a = local - it.js * it.H;
+  it.base = m.off[it.n];
+  it.q_row0 = q - it.a;
+  return it;
+}
+
+// 16-bit sampled mask of chunk c (filters 16c..16c+15) of pixel (a, col).
+__device__ __forceinline__ uint32_t chunk_mask(const uint32_t *bits, int KW, const Item &it, int a,
+                                               int col, int c) {
+  if (col >= it.W || a < 0 || a >= it.H) return 0u;
+  int64_t pix = it.base + (int64_t)a * it.W + col;
+  return (bits[pix * KW + (c >> 1)] >> ((c & 1) * 16)) & 0xFFFFu;
+}
+
+// Exclusive scan of one int per thread over a 128-thread block.
+__device__ __forceinline__ int scan128(int v, int *sh, int &total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  int pre = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) pre += (i < w) ? sh[i] : 0;
+  total = sh[0] + sh[1] + sh[2] + sh[3];
+  __syncthreads();
+  return pre + x - v;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t *>(&h);
+}
+
+// ------------------------------------------------------------------ filter images
+// B operand of the adjoint: per tap row u a [Kp filters x 16 taps] K-major
+// tile; core (filter group g, tap half j) at u*Kp*32 + j*Kp*16 + g*128.
+// B operand of the synthesis: [16 s taps x Kp filters] K-major; core (tap
+// group T, filter chunk j) at j*(2 s*128) + T*128; tap n = 16 u + v.
+__global__ void prep_filters_kernel(const float *d, int K, int S, int Kp, __nv_bfloat16 *badj,
+                                    __nv_bfloat16 *bsyn) {
+  const int M = S * S;
+  const int n_adj = S * Kp * 16;
+  const int n_syn = Kp * 16 * S;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_adj + n_syn;
+       i += gridDim.x * blockDim.x) {
+    if (i < n_adj) {
+      int e = i & 7, r = (i >> 3) & 7, rest = i >> 6;  // rest = (u*2 + j)*(Kp/8) + g
+      int g = rest % (Kp / 8), uj = rest / (Kp / 8);
+      int j = uj & 1, u = uj >> 1;
+      int k = 8 * g + r, v = 8 * j + e;
+      float val = (k < K && v < S) ? d[(int64_t)k * M + u * S + v] : 0.0f;
+      badj[i] = __float2bfloat16_rn(val);
+    } else {
+      int t = i - n_adj;
+      int e = t & 7, r = (t >> 3) & 7, rest = t >> 6;  // rest = j*(2S) + T
+      int T = rest % (2 * S), j = rest / (2 * S);
+      int n = 8 * T + r, k = 8 * j + e;
+      int u = n >> 4, v = n & 15;
+      float val = (k < K && v < S) ? d[(int64_t)k * M + u * S + v] : 0.0f;
+      bsyn[t] = __float2bfloat16_rn(val);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ packed layout
+
+__global__ void __launch_bounds__(kThreads) seg_count_kernel(ItemMap im, int KW, int NC,
+                                                             const uint32_t *bits,
+                                                             uint32_t *counts) {
+  __shared__ int sh[4];
+  const int q = blockIdx.x;
+  const Item it = item_of(im, q);
+  const int col = it.js * kStrip + threadIdx.x;
+  for (int c = 0; c < NC; ++c) {
+    int cnt = __popc(chunk_mask(bits, KW, it, it.a, col, c));
+    int total;
+    scan128(cnt, sh, total);
+    if (threadIdx.x == 0) counts[(int64_t)q * NC + c] = (uint32_t)total;
+  }
+}
+
+// Exclusive scan u32 -> u64 in three passes over blocks of 1024 elements.
+__global__ void scan_local_kernel(const uint32_t *in, uint64_t *out, int n, uint64_t *block_sums) {
+  __shared__ uint64_t sh[32];
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  uint64_t v = i < n ? in[i] : 0, x = v;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint64_t s = sh[lane], t = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    sh[lane] = t - s;
+    if (lane == 31) block_sums[blockIdx.x] = t;
+  }
+  __syncthreads();
+  if (i < n) out[i] = sh[w] + x - v;
+}
+
+__global__ void scan_blocks_kernel(uint64_t *block_sums, int nb, uint64_t *total_out) {
+  if (threadIdx.x != 0) return;
+  uint64_t run = 0;
+  for (int i = 0; i < nb; ++i) {
+    uint64_t s = block_sums[i];
+    block_sums[i] = run;
+    run += s;
+  }
+  *total_out = run;
+}
+
+__global__ void scan_add_kernel(uint64_t *out, int n, const uint64_t *block_sums) {
+  const int i = blockIdx.x * 1024 + threadIdx.x;
+  if (i < n) out[i] += block_sums[blockIdx.x];
+}
+
+// mode 0: packed <- z on the sampled set (warm start)
+// mode 1: z <- packed on the sampled set, 0 elsewhere (Eq. 4)
+__global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int KW, int NC,
+                                                        const uint32_t *bits,
+                                                        const uint64_t *seg_base, float *packed,
+                                                        float *z, int mode) {
+  __shared__ int sh[4];
+  const int q = blockIdx.x;
+  const Item it = item_of(im, q);
+  const int col = it.js * kStrip + threadIdx.x;
+  const bool inside = col < it.W;
+  const int64_t pix = it.base + (int64_t)it.a * it.W + col;
+  for (int c = 0; c < NC; ++c) {
+    uint32_t m = chunk_mask(bits, KW, it, it.a, col, c);
+    int total;
+    int off = scan128(__popc(m), sh, total);
+    float *seg = packed + seg_base[(int64_t)q * NC + c] + off;
+    int rank = 0;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      int k = 16 * c + e;
+      if (!inside || k >= K) continue;
+      if ((m >> e) & 1u) {
+        if (mode == 0) seg[rank] = z[pix * K + k];
+        else z[pix * K + k] = seg[rank];
+        ++rank;
+      } else if (mode == 1) {
+        z[pix * K + k] = 0.0f;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ synthesis
+
+template <int S>
+struct SynthSmem {
+  static constexpr int C = (S - 1) / 2;
+  static constexpr int N = 16 * S;
+  __host__ __device__ static size_t a_bytes(int Kp) { return (size_t)kStrip * Kp * 2; }
+  __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)N * Kp * 2; }
+  __host__ __device__ static size_t total(int Kp) {
+    return 1024 + a_bytes(Kp) + b_bytes(Kp) + (size_t)kStrip * 16 * 4 +
+           (size_t)2 * S * kPuRow * 4;
+  }
+};
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, int Kp, int KW,
+                                                            const uint32_t *__restrict__ bits,
+                                                            const uint64_t *__restrict__ seg_base,
+                                                            const float *__restrict__ packed,
+                                                            const uint4 *__restrict__ bsyn,
+                                                            float *__restrict__ xcore,
+                                                            float *__restrict__ spill, int *err) {
+  using L = SynthSmem<S>;
+  constexpr int C = L::C, N = L::N;
+  const int NC = Kp / 16;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *As = smem;
+  uint8_t *Bs = As + L::a_bytes(Kp);
+  float *stage = reinterpret_cast<float *>(Bs + L::b_bytes(Kp));
+  float *Pu = stage + kStrip * 16;  // [2][S][kPuRow]
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int sh[4];
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 256);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::fence_mbar_init();
+  }
+  {
+    const int n16 = (int)(L::b_bytes(Kp) / 16);
+    uint4 *dst = reinterpret_cast<uint4 *>(Bs);
+    for (int i = tid; i < n16; i += kThreads) dst[i] = bsyn[i];
+    for (int i = tid; i < 2 * S * kPuRow; i += kThreads) Pu[i] = 0.0f;
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base;
+  const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16);
+  const uint32_t idesc = tc::idesc_bf16_f32(128, N);
+  const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
+  const uint32_t b_lbo = 2 * S * 128;
+  uint32_t phase = 0;
+  bool failed = false;
+
+  const int Q = im.total;
+  int q = (int)((int64_t)Q * blockIdx.x / gridDim.x);
+  const int q_end = (int)((int64_t)Q * (blockIdx.x + 1) / gridDim.x);
+  const int i = tid;  // pixel lane
+  while (q < q_end && !failed) {
+    const Item it = item_of(im, q);
+    const int seg_end = min(q_end, it.q_row0 + it.H);
+    const int o0 = it.a, o1 = o0 + (seg_end - q);
+    const int a_start = max(0, o0 - C), a_end = min(it.H, o1 + C);
+    const int b0 = it.js * kStrip;
+    float acc[S], acch[S];
+#pragma unroll
+    for (int u = 0; u < S; ++u) acc[u] = acch[u] = 0.0f;
+    const bool halo = i < 2 * C;
+    const int hcol = i < C ? i - C : kStrip + i - C;  // halo output column (strip-local)
+
+    for (int a = a_start; a < a_end; ++a) {
+      const int qa = it.q_row0 + a;
+      // 1. expand the packed codes of code row a into the A operand (BF16)
+      for (int c = 0; c < NC; ++c) {
+        uint32_t m = chunk_mask(bits, KW, it, a, b0 + i, c);
+        int total;
+        int off = scan128(__popc(m), sh, total);
+        const float *src = packed + seg_base[(int64_t)qa * NC + c];
+        for (int j = tid; j < total; j += kThreads) stage[j] = src[j];
+        __syncthreads();
+        float v[16];
+        int rank = 0;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          v[e] = ((m >> e) & 1u) ? stage[off + rank] : 0.0f;
+          rank += (m >> e) & 1u;
+        }
+        uint4 lo = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                              pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+        uint4 hi = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
+                              pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+        uint8_t *dst = As + (size_t)(2 * c) * 2048 + (i >> 3) * 128 + (i & 7) * 16;
+        *reinterpret_cast<uint4 *>(dst) = lo;
+        *reinterpret_cast<uint4 *>(dst + 2048) = hi;
+        __syncthreads();
+      }
+      tc::fence_proxy_async();
+      __syncthreads();
+      // 2. P = Z_row * D^T over all filter chunks
+      if (tid == 0) {
+        tc::fence_after_sync();
+        for (int kk = 0; kk < NC; ++kk) {
+          uint64_t ad = tc::smem_desc(a_base + kk * 2 * 2048, 2048, 128);
+          uint64_t bd = tc::smem_desc(b_base + kk * 2 * b_lbo, b_lbo, 128);
+          tc::mma_bf16(taddr, ad, bd, idesc, kk > 0 ? 1u : 0u);
+        }
+        tc::mma_commit(&mbar);
+      }
+      bool ok = tc::mbar_wait_bounded(&mbar, phase, kWaitNs);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(err, 1);
+        failed = true;
+        break;
+      }
+      tc::fence_after_sync();
+      // 3. col2im: output row a-c+u gets sum_v P[b + c - v][(u, v)]
+#pragma unroll
+      for (int u = 0; u < S; ++u) {
+        float p[16];
+        tc::tmem_ld16(lane_addr + 16 * u, p);
+        float *pu = Pu + (u & 1) * S * kPuRow;
+#pragma unroll
+        for (int v = 0; v < S; ++v) pu[v * kPuRow + i + kPad] = p[v];
+        __syncthreads();
+        float sum = 0.0f;
+#pragma unroll
+        for (int v = 0; v < S; ++v) sum += pu[v * kPuRow + i + C + kPad - v];
+        acc[u] += sum;
+        if (halo) {
+          float hs = 0.0f;
+#pragma unroll
+          for (int v = 0; v < S; ++v) hs += pu[v * kPuRow + hcol + C + kPad - v];
+          acch[u] += hs;
+        }
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+      // 4. output row a - c is complete
+      const int o = a - C;
+      if (o >= o0 && o < o1) {
+        if (b0 + i < it.W) xcore[it.base + (int64_t)o * it.W + b0 + i] = acc[0];
+        if (halo) spill[(int64_t)(it.q_row0 + o) * (2 * C) + i] = acch[0];
+      }
+#pragma unroll
+      for (int u = 0; u < S - 1; ++u) {
+        acc[u] = acc[u + 1];
+        acch[u] = acch[u + 1];
+      }
+      acc[S - 1] = acch[S - 1] = 0.0f;
+    }
+    if (failed) break;
+    // rows whose remaining contributors lie below the image
+#pragma unroll
+    for (int j = 0; j < S - 1; ++j) {
+      const int o = a_end - C + j;
+      if (o >= o0 && o < o1 && o < it.H) {
+        if (b0 + i < it.W) xcore[it.base + (int64_t)o * it.W + b0 + i] = acc[j];
+        if (halo) spill[(int64_t)(it.q_row0 + o) * (2 * C) + i] = acch[j];
+      }
+    }
+    q = seg_end;
+  }
+  if (failed) {
+    // let any MMA still in flight finish before the TMEM is released
+    tc::mbar_wait_bounded(&mbar, phase, kWaitNs);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, 256);
+  }
+}
+
+// r = xcore + spills of the neighbouring strips - x
+__global__ void finalize_r_kernel(BatchDev b, ItemMap im, int C, const float *__restrict__ xcore,
+                                  const float *__restrict__ spill, const float *__restrict__ x,
+                                  float *__restrict__ r) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < b.total_px;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    int n = upper_index(b.off, b.n, p);
+    int64_t local = p - b.off[n];
+    int W = b.W[n], H = b.H[n];
+    int o = (int)(local / W), col = (int)(local - (int64_t)o * W);
+    int js = col / kStrip, lc = col - js * kStrip, JS = (W + kStrip - 1) / kStrip;
+    float v = xcore[p];
+    if (C > 0) {
+      if (lc < C && js > 0) v += spill[(int64_t)(im.item0[n] + (js - 1) * H + o) * (2 * C) + C + lc];
+      if (lc >= kStrip - C && js + 1 < JS)
+        v += spill[(int64_t)(im.item0[n] + (js + 1) * H + o) * (2 * C) + lc - (kStrip - C)];
+    }
+    r[p] = v - x[p];
+  }
+}
+
+// ------------------------------------------------------------------ adjoint + prox
+
+template <int S>
+struct AdjSmem {
+  static constexpr int C = (S - 1) / 2;
+  static constexpr int kSRow = 17 * 128;  // one Toeplitz residual row (17 blocks)
+  __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)S * Kp * 32; }
+  __host__ __device__ static size_t total(int Kp) {
+    return 1024 + b_bytes(Kp) + (size_t)S * kSRow + 144 * 4 + (size_t)kStrip * 16 * 4;
+  }
+};
+
+__host__ __device__ inline int tmem_cols_for(int n) {
+  int c = 32;
+  while (c < n) c <<= 1;
+  return c;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int Kp, int KW,
+                                                          const uint32_t *__restrict__ bits,
+                                                          const uint64_t *__restrict__ seg_base,
+                                                          float *__restrict__ packed,
+                                                          const uint4 *__restrict__ badj,
+                                                          const float *__restrict__ r,
+                                                          const StepParams *__restrict__ prm,
+                                                          int *err) {
+  using L = AdjSmem<S>;
+  constexpr int C = L::C;
+  const int NC = Kp / 16;
+  const int tcols = tmem_cols_for(Kp);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *Bs = smem;
+  uint8_t *ring = Bs + L::b_bytes(Kp);
+  float *rstage = reinterpret_cast<float *>(ring + (size_t)S * L::kSRow);
+  float *stage = rstage + 144;
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int sh[4];
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, tcols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::fence_mbar_init();
+  }
+  {
+    const int n16 = (int)(L::b_bytes(Kp) / 16);
+    uint4 *dst = reinterpret_cast<uint4 *>(Bs);
+    for (int i = tid; i < n16; i += kThreads) dst[i] = badj[i];
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base;
+  const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16);
+  const uint32_t idesc = tc::idesc_bf16_f32(128, Kp);
+  const uint32_t ring_base = tc::smem_u32(ring), b_base = tc::smem_u32(Bs);
+  const float alpha = prm->alpha, thr = prm->thresh;
+  uint32_t phase = 0;
+  bool failed = false;
+
+  // Toeplitz row of residual row ar into its ring slot:
+  // slot[g][i][e] = r(ar, b0 - c + 8 g + i + e), g < 17, i, e < 8.
+  auto build_row = [&](const Item &it, int ar) {
+    const int b0 = it.js * kStrip;
+    for (int j = tid; j < 144; j += kThreads) {
+      int col = b0 - C + j;
+      float v = 0.0f;
+      if (ar >= 0 && ar < it.H && col >= 0 && col < it.W)
+        v = r[it.base + (int64_t)ar * it.W + col];
+      rstage[j] = v;
+    }
+    __syncthreads();
+    uint8_t *slot = ring + (size_t)(((ar % S) + S) % S) * L::kSRow;
+    for (int t = tid; t < 17 * 8; t += kThreads) {
+      int g = t >> 3, ii = t & 7;
+      const float *src = rstage + 8 * g + ii;
+      uint4 w = make_uint4(pack_bf16x2(src[0], src[1]), pack_bf16x2(src[2], src[3]),
+                           pack_bf16x2(src[4], src[5]), pack_bf16x2(src[6], src[7]));
+      *reinterpret_cast<uint4 *>(slot + g * 128 + ii * 16) = w;
+    }
+    __syncthreads();
+  };
+
+  const int Q = im.total;
+  int q = (int)((int64_t)Q * blockIdx.x / gridDim.x);
+  const int q_end = (int)((int64_t)Q * (blockIdx.x + 1) / gridDim.x);
+  const int i = tid;
+  while (q < q_end && !failed) {
+    const Item it0 = item_of(im, q);
+    const int seg_end = min(q_end, it0.q_row0 + it0.H);
+    const int o0 = it0.a, o1 = o0 + (seg_end - q);
+    const int b0 = it0.js * kStrip;
+    for (int ar = o0 - C; ar < o0 + C; ++ar) build_row(it0, ar);
+    for (int a = o0; a < o1; ++a) {
+      const int qa = it0.q_row0 + a;
+      build_row(it0, a + C);
+      tc::fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        for (int u = 0; u < S; ++u) {
+          int ar = a - C + u;
+          uint32_t slot = (uint32_t)(((ar % S) + S) % S) * L::kSRow;
+          uint64_t ad = tc::smem_desc(ring_base + slot, 128, 128);
+          uint64_t bd = tc::smem_desc(b_base + u * Kp * 32, Kp * 16, 128);
+          tc::mma_bf16(taddr, ad, bd, idesc, u > 0 ? 1u : 0u);
+        }
+        tc::mma_commit(&mbar);
+      }
+      bool ok = tc::mbar_wait_bounded(&mbar, phase, kWaitNs);
+      phase ^= 1u;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(err, 1);
+        failed = true;
+        break;
+      }
+      tc::fence_after_sync();
+      // prox on the packed sampled codes of this item, chunk by chunk
+      for (int c = 0; c < NC; ++c) {
+        uint32_t m = chunk_mask(bits, KW, it0, a, b0 + i, c);
+        int total;
+        int off = scan128(__popc(m), sh, total);
+        float *seg = packed + seg_base[(int64_t)qa * NC + c];
+        for (int j = tid; j < total; j += kThreads) stage[j] = seg[j];
+        float g[16];
+        tc::tmem_ld16(lane_addr + 16 * c, g);
+        __syncthreads();
+        int rank = off;
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          if ((m >> e) & 1u) {
+            stage[rank] = soft_threshold(stage[rank] - alpha * g[e], thr);
+            ++rank;
+          }
+        }
+        __syncthreads();
+        for (int j = tid; j < total; j += kThreads) seg[j] = stage[j];
+        __syncthreads();
+      }
+      tc::fence_before_sync();
+      __syncthreads();
+    }
+    q = seg_end;
+  }
+  if (failed) tc::mbar_wait_bounded(&mbar, phase, kWaitNs);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, tcols);
+  }
+}
+
+// ------------------------------------------------------------------ self-test GEMM
+// D[128 x N] = A[128 x 64] B[N x 64]^T; canonical K-major layouts with
+// LBO = rows * 16 bytes (K-direction core stride) and SBO = 128 bytes.
+__global__ void __launch_bounds__(kThreads) selftest_gemm_kernel(int N, const float *A,
+                                                                 const float *B, float *D,
+                                                                 int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *As = smem;                  // 128 x 64 bf16 = 16 KB
+  uint8_t *Bs = smem + 128 * 64 * 2;   // N x 64 bf16
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 256);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::fence_mbar_init();
+  }
+  // element (row, k) -> (k/8)*(rows*16) + (row/8)*128 + (row%8)*16 + (k%8)*2
+  for (int t = tid; t < 128 * 64; t += kThreads) {
+    int row = t / 64, k = t % 64;
+    size_t o = (size_t)(k / 8) * (128 * 16) + (row / 8) * 128 + (row % 8) * 16 + (k % 8) * 2;
+    *reinterpret_cast<__nv_bfloat16 *>(As + o) = __float2bfloat16_rn(A[t]);
+  }
+  for (int t = tid; t < N * 64; t += kThreads) {
+    int row = t / 64, k = t % 64;
+    size_t o = (size_t)(k / 8) * (N * 16) + (row / 8) * 128 + (row % 8) * 16 + (k % 8) * 2;
+    *reinterpret_cast<__nv_bfloat16 *>(Bs + o) = __float2bfloat16_rn(B[t]);
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base;
+  if (tid == 0) {
+    const uint32_t idesc = tc::idesc_bf16_f32(128, N);
+    for (int kk = 0; kk < 4; ++kk) {
+      uint64_t ad = tc::smem_desc(tc::smem_u32(As) + kk * 2 * 128 * 16, 128 * 16, 128);
+      uint64_t bd = tc::smem_desc(tc::smem_u32(Bs) + kk * 2 * N * 16, N * 16, 128);
+      tc::mma_bf16(taddr, ad, bd, idesc, kk > 0 ? 1u : 0u);
+    }
+    tc::mma_commit(&mbar);
+  }
+  bool ok = tc::mbar_wait_bounded(&mbar, 0, kWaitNs);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(err, 1);
+    tc::mbar_wait_bounded(&mbar, 0, kWaitNs);
+  } else {
+    tc::fence_after_sync();
+    const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16);
+    for (int c = 0; c < N; c += 16) {
+      float v[16];
+      tc::tmem_ld16(lane_addr + c, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) D[(size_t)tid * N + c + e] = v[e];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, 256);
+  }
+}
+
+// ------------------------------------------------------------------ host helpers
+
+template <typename F>
+cudaError_t dispatch_s(int s, F &&f) {
+  switch (s) {
+    case 1: return f(std::integral_constant<int, 1>());
+    case 3: return f(std::integral_constant<int, 3>());
+    case 5: return f(std::integral_constant<int, 5>());
+    case 7: return f(std::integral_constant<int, 7>());
+    case 9: return f(std::integral_constant<int, 9>());
+    case 11: return f(std::integral_constant<int, 11>());
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t ensure(TcWorkspace::Buf &b, size_t need) {
+  if (need <= b.bytes) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  size_t want = need + need / 8 + 256;
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e == cudaSuccess) b.bytes = want;
+  return e;
+}
+
+template <typename T>
+T *as(const TcWorkspace::Buf &b) {
+  return reinterpret_cast<T *>(b.p);
+}
+
+#define TRY(expr)                            \
+  do {                                       \
+    cudaError_t e_ = (expr);                 \
+    if (e_ != cudaSuccess) return e_;        \
+  } while (0)
+
+}  // namespace
+
+int *tc_error_word(TcWorkspace &ws) {
+  if (ensure(ws.err, sizeof(int)) != cudaSuccess) return nullptr;
+  return as<int>(ws.err);
+}
+
+const char *tc_last_error(const TcWorkspace &ws) { return ws.last_error.c_str(); }
+
+void tc_release(TcWorkspace &ws) {
+  for (TcWorkspace::Buf *b : {&ws.item0, &ws.seg_count, &ws.seg_base, &ws.scan_blocks, &ws.packed,
+                              &ws.xcore, &ws.spill, &ws.r, &ws.badj, &ws.bsyn, &ws.err}) {
+    if (b->p) cudaFree(b->p);
+    b->p = nullptr;
+    b->bytes = 0;
+  }
+}
+
+cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, const int *W_host,
+                         int K, int s, const float *x, const float *d, float *z,
+                         const uint32_t *bits, const StepParams *prm, int n_iters,
+                         cudaStream_t st) {
+  if (K > 256) {
+    ws.last_error = "the tensor path supports K <= 256";
+    return cudaErrorNotSupported;
+  }
+  const int Kp = (K + 15) / 16 * 16, NC = Kp / 16, KW = (K + 31) / 32, C = (s - 1) / 2;
+  if (ws.sm_count == 0) {
+    int dev;
+    TRY(cudaGetDevice(&dev));
+    TRY(cudaDeviceGetAttribute(&ws.sm_count, cudaDevAttrMultiProcessorCount, dev));
+  }
+  // row-item map (host, cached per batch shape)
+  const int n = b.n;
+  std::vector<int> Hh(H_host, H_host + n), Wh(W_host, W_host + n);
+  if (Hh != ws.host_H || Wh != ws.host_W) {
+    std::vector<int> item0(n + 1);
+    int64_t q = 0;
+    for (int i = 0; i < n; ++i) {
+      item0[i] = (int)q;
+      q += (int64_t)Hh[i] * ((Wh[i] + kStrip - 1) / kStrip);
+    }
+    if (q > 0x7fffffff) {
+      ws.last_error = "batch has too many row items";
+      return cudaErrorNotSupported;
+    }
+    item0[n] = (int)q;
+    TRY(ensure(ws.item0, (size_t)(n + 1) * 4));
+    TRY(cudaMemcpyAsync(ws.item0.p, item0.data(), (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, st));
+    TRY(cudaStreamSynchronize(st));  // the host vector is released after this call
+    ws.host_item0.swap(item0);
+    ws.host_H.swap(Hh);
+    ws.host_W.swap(Wh);
+    ws.n_items = (int)q;
+  }
+  const int Q = ws.n_items;
+  ItemMap im{n, as<int>(ws.item0), b.H, b.W, b.off, Q};
+  const int64_t nseg = (int64_t)Q * NC;
+  const int nblk = (int)((nseg + 1023) / 1024);
+  TRY(ensure(ws.seg_count, (size_t)nseg * 4));
+  TRY(ensure(ws.seg_base, (size_t)(nseg + 1) * 8));
+  TRY(ensure(ws.scan_blocks, (size_t)(nblk + 1) * 8));
+  TRY(ensure(ws.packed, (size_t)b.total_px * K * 4 + 16));
+  TRY(ensure(ws.xcore, (size_t)b.total_px * 4));
+  TRY(ensure(ws.r, (size_t)b.total_px * 4));
+  TRY(ensure(ws.spill, (size_t)Q * (2 * C > 0 ? 2 * C : 1) * 4));
+  TRY(ensure(ws.badj, (size_t)s * Kp * 32));
+  TRY(ensure(ws.bsyn, (size_t)Kp * 16 * s * 2));
+  TRY(ensure(ws.err, sizeof(int)));
+
+  // filter operand images, sampled-code layout, warm start
+  prep_filters_kernel<<<64, 256, 0, st>>>(d, K, s, Kp, as<__nv_bfloat16>(ws.badj),
+                                          as<__nv_bfloat16>(ws.bsyn));
+  TRY(cudaGetLastError());
+  if (Q == 0) return cudaSuccess;
+  seg_count_kernel<<<Q, kThreads, 0, st>>>(im, KW, NC, bits, as<uint32_t>(ws.seg_count));
+  TRY(cudaGetLastError());
+  uint64_t *seg_base = as<uint64_t>(ws.seg_base);
+  scan_local_kernel<<<nblk, 1024, 0, st>>>(as<uint32_t>(ws.seg_count), seg_base, (int)nseg,
+                                           as<uint64_t>(ws.scan_blocks));
+  TRY(cudaGetLastError());
+  scan_blocks_kernel<<<1, 32, 0, st>>>(as<uint64_t>(ws.scan_blocks), nblk, seg_base + nseg);
+  TRY(cudaGetLastError());
+  scan_add_kernel<<<nblk, 1024, 0, st>>>(seg_base, (int)nseg, as<uint64_t>(ws.scan_blocks));
+  TRY(cudaGetLastError());
+  int pr = ws.prof ? ws.prof->begin(KID_PACK, st) : -1;
+  pack_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, as<float>(ws.packed), z, 0);
+  TRY(cudaGetLastError());
+  if (ws.prof) ws.prof->end(pr, st);
+
+  TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
+    constexpr int S = decltype(SC)::value;
+    const size_t smem_syn = SynthSmem<S>::total(Kp), smem_adj = AdjSmem<S>::total(Kp);
+    auto ks = synth_tc_kernel<S>;
+    auto ka = adj_tc_kernel<S>;
+    TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_syn));
+    TRY(cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_adj));
+    int occ_s = 0, occ_a = 0;
+    TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, ks, kThreads, smem_syn));
+    TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, ka, kThreads, smem_adj));
+    occ_s = std::max(1, std::min(occ_s, 512 / 256));
+    occ_a = std::max(1, std::min(occ_a, 512 / tmem_cols_for(Kp)));
+    const int grid_s = std::min(Q, ws.sm_count * occ_s);
+    const int grid_a = std::min(Q, ws.sm_count * occ_a);
+    const int fin_grid = (int)std::min<int64_t>((b.total_px + 255) / 256, 152 * 16);
+    for (int it = 0; it < n_iters; ++it) {
+      int p1 = ws.prof ? ws.prof->begin(KID_SYNTH_TC, st) : -1;
+      ks<<<grid_s, kThreads, smem_syn, st>>>(im, K, Kp, KW, bits, seg_base, as<float>(ws.packed),
+                                            as<uint4>(ws.bsyn), as<float>(ws.xcore),
+                                            as<float>(ws.spill), as<int>(ws.err));
+      TRY(cudaGetLastError());
+      if (ws.prof) ws.prof->end(p1, st);
+      int p2 = ws.prof ? ws.prof->begin(KID_FINALIZE, st) : -1;
+      finalize_r_kernel<<<fin_grid, 256, 0, st>>>(b, im, C, as<float>(ws.xcore),
+                                                   as<float>(ws.spill), x, as<float>(ws.r));
+      TRY(cudaGetLastError());
+      if (ws.prof) ws.prof->end(p2, st);
+      int p3 = ws.prof ? ws.prof->begin(KID_ADJ_TC, st) : -1;
+      ka<<<grid_a, kThreads, smem_adj, st>>>(im, K, Kp, KW, bits, seg_base, as<float>(ws.packed),
+                                            as<uint4>(ws.badj), as<float>(ws.r), prm,
+                                            as<int>(ws.err));
+      TRY(cudaGetLastError());
+      if (ws.prof) ws.prof->end(p3, st);
+    }
+    return cudaSuccess;
+  }));
+  // Eq. 4: dense codes, zero off the sampled set
+  int pu = ws.prof ? ws.prof->begin(KID_UNPACK, st) : -1;
+  pack_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, as<float>(ws.packed), z, 1);
+  TRY(cudaGetLastError());
+  if (ws.prof) ws.prof->end(pu, st);
+  return cudaSuccess;
+}
+
+cudaError_t tc_selftest_gemm(int N, const float *A, const float *B, float *D, int *err,
+                             cudaStream_t st) {
+  if (N < 16 || N > 256 || N % 16 != 0) return cudaErrorInvalidValue;
+  size_t smem = 1024 + 128 * 64 * 2 + (size_t)N * 64 * 2;
+  TRY(cudaFuncSetAttribute(selftest_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem));
+  selftest_gemm_kernel<<<1, kThreads, smem, st>>>(N, A, B, D, err);
+  return cudaGetLastError();
+}
+
+}  // namespace scsc

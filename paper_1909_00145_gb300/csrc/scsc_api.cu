@@ -1,0 +1,636 @@
+// scsc_api.cu -- the C ABI (include/scsc.h): argument checking, workspace
+// ownership, batch descriptors and the orchestration of the kernels for the
+// code step (Eq. 3, Eq. 4), the dictionary steps (Eq. 5, Eq. 7-8), the
+// objective (Eq. 1) and the differentiation primitives.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/scsc.h"
+#include "../../include/scsc_diag.h"
+#include "scsc_internal.cuh"
+#include "profiler.cuh"
+#include "scsc_tc.cuh"
+
+using namespace scsc;
+
+namespace {
+
+constexpr int kPowerIters = 50;        // normalised applications before the Rayleigh quotient
+constexpr double kSafety = 1.01;       // L = 1.01 x estimate
+constexpr uint64_t kTagLz = 0x4C;      // start-vector tags of the three power iterations
+constexpr uint64_t kTagLd = 0x44;
+constexpr uint64_t kTagLc = 0x43;
+constexpr int kRedBlocks = 1024;       // blocks of the FP64 reductions (fixed: deterministic)
+constexpr int kGradGroups = 304;       // block rows of the filter-gradient reduction (2 x 152 SMs)
+constexpr uint32_t kStateMagic = 0x43534353u;  // "SCSC"
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t need) {
+    if (need <= bytes) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    size_t want = need + need / 8;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e == cudaSuccess) bytes = want;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Host copy of a batch descriptor plus its device image.
+struct BatchCache {
+  std::vector<unsigned char> host;  // serialised descriptor (compare key)
+  void *pinned = nullptr;
+  size_t pinned_bytes = 0;
+  DevBuf dev;
+  BatchDev view{};
+  int maxH = 0, maxW = 0;
+  cudaEvent_t copied = nullptr;
+};
+
+}  // namespace
+
+struct scsc_ctx {
+  scsc_config cfg{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  BatchCache batch, domain;     // the call's batch; the step-size domain
+  int domainH = -1, domainW = -1;
+  DevBuf bits, r, pix2, prm, scal, partials, gpart, gsum, pu, pw, pcodes, flag;
+  // tensor path
+  TcWorkspace tc;
+  // online surrogates
+  DevBuf C, B, Cd;
+  uint64_t online_t = 0;
+  Profiler prof;
+};
+
+namespace {
+
+scsc_status fail(scsc_ctx *c, scsc_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+#define CK(expr)                                                                    \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? SCSC_ENOMEM : SCSC_ECUDA,  \
+                  "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define CKS(expr)                  \
+  do {                             \
+    scsc_status s_ = (expr);       \
+    if (s_ != SCSC_OK) return s_;  \
+  } while (0)
+
+int64_t tiles_of(int H, int W) { return (int64_t)((H + 31) / 32) * ((W + 31) / 32); }
+
+// Validate the host arrays of a batch and stage them on the device.
+scsc_status upload_batch(scsc_ctx *ctx, BatchCache &bc, int n, const int64_t *off, const int *H,
+                         const int *W, const int64_t *ids) {
+  if (n < 1) return fail(ctx, SCSC_EINVAL, "batch: n_images must be >= 1 (got %d)", n);
+  if (!off || !H || !W || !ids) return fail(ctx, SCSC_EINVAL, "batch: NULL array");
+  std::vector<int64_t> o(n + 1);
+  std::vector<int> t0(n + 1);
+  int64_t pos = 0, tiles = 0;
+  int mh = 0, mw = 0;
+  for (int i = 0; i < n; ++i) {
+    if (H[i] < 1 || W[i] < 1 || H[i] > 65536 || W[i] > 65536)
+      return fail(ctx, SCSC_EINVAL, "batch: image %d has size %dx%d", i, H[i], W[i]);
+    if (off[i] != pos)
+      return fail(ctx, SCSC_EINVAL,
+                  "batch: offsets[%d] = %lld, images must be packed back to back (expected %lld)",
+                  i, (long long)off[i], (long long)pos);
+    if (ids[i] < 0) return fail(ctx, SCSC_EINVAL, "batch: image_ids[%d] < 0", i);
+    o[i] = pos;
+    t0[i] = (int)tiles;
+    pos += (int64_t)H[i] * W[i];
+    tiles += tiles_of(H[i], W[i]);
+    if (tiles > (int64_t)0x7fffffff) return fail(ctx, SCSC_EINVAL, "batch too large");
+    mh = H[i] > mh ? H[i] : mh;
+    mw = W[i] > mw ? W[i] : mw;
+  }
+  o[n] = pos;
+  t0[n] = (int)tiles;
+  // layout: off[n+1] i64 | ids[n] i64 | H[n] i32 | W[n] i32 | tile0[n+1] i32
+  size_t bytes = (size_t)(n + 1) * 8 + (size_t)n * 8 + (size_t)n * 4 * 2 + (size_t)(n + 1) * 4;
+  std::vector<unsigned char> ser(bytes);
+  unsigned char *q = ser.data();
+  memcpy(q, o.data(), (n + 1) * 8);
+  q += (n + 1) * 8;
+  memcpy(q, ids, n * 8);
+  q += n * 8;
+  memcpy(q, H, n * 4);
+  q += n * 4;
+  memcpy(q, W, n * 4);
+  q += n * 4;
+  memcpy(q, t0.data(), (n + 1) * 4);
+  if (bc.host == ser && bc.dev.p) return SCSC_OK;  // unchanged: reuse the device copy
+  if (!bc.copied) CK(cudaEventCreateWithFlags(&bc.copied, cudaEventDisableTiming));
+  CK(cudaEventSynchronize(bc.copied));  // the previous staging copy has landed
+  if (bc.pinned_bytes < bytes) {
+    if (bc.pinned) cudaFreeHost(bc.pinned);
+    bc.pinned = nullptr;
+    bc.pinned_bytes = 0;
+    CK(cudaMallocHost(&bc.pinned, bytes));
+    bc.pinned_bytes = bytes;
+  }
+  memcpy(bc.pinned, ser.data(), bytes);
+  CK(bc.dev.ensure(bytes));
+  CK(cudaMemcpyAsync(bc.dev.p, bc.pinned, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaEventRecord(bc.copied, ctx->stream));
+  bc.host.swap(ser);
+  unsigned char *d = bc.dev.as<unsigned char>();
+  bc.view.n = n;
+  bc.view.off = reinterpret_cast<const int64_t *>(d);
+  bc.view.ids = reinterpret_cast<const int64_t *>(d + (n + 1) * 8);
+  bc.view.H = reinterpret_cast<const int *>(d + (n + 1) * 8 + n * 8);
+  bc.view.W = reinterpret_cast<const int *>(d + (n + 1) * 8 + n * 8 + n * 4);
+  bc.view.tile0 = reinterpret_cast<const int *>(d + (n + 1) * 8 + n * 8 + n * 8);
+  bc.view.total_px = pos;
+  bc.view.n_tiles = (int)tiles;
+  bc.maxH = mh;
+  bc.maxW = mw;
+  return SCSC_OK;
+}
+
+scsc_status stage_batch(scsc_ctx *ctx, const scsc_batch *b) {
+  if (!b) return fail(ctx, SCSC_EINVAL, "batch is NULL");
+  return upload_batch(ctx, ctx->batch, b->n_images, b->offsets, b->H, b->W, b->image_ids);
+}
+
+int KW_of(const scsc_ctx *ctx) { return (ctx->cfg.K + 31) / 32; }
+int M_of(const scsc_ctx *ctx) { return ctx->cfg.s * ctx->cfg.s; }
+
+uint64_t threshold_T(const scsc_config &c) {
+  return ((uint64_t)c.p_num << 32) / (uint64_t)c.p_den;
+}
+
+scsc_status build_mask(scsc_ctx *ctx, uint64_t t) {
+  const BatchDev &b = ctx->batch.view;
+  CK(ctx->bits.ensure((size_t)b.total_px * KW_of(ctx) * 4));
+  int pr = ctx->prof.begin(KID_MASK, ctx->stream);
+  CK(launch_mask_bits(b, ctx->cfg.K, ctx->cfg.seed, t, threshold_T(ctx->cfg),
+                      ctx->bits.as<uint32_t>(), ctx->stream));
+  ctx->prof.end(pr, ctx->stream);
+  return SCSC_OK;
+}
+
+// Operator D D^T on the step-size domain: u (pixels) -> w (pixels).
+scsc_status apply_ddt(scsc_ctx *ctx, const float *d, const float *u, float *w) {
+  const BatchDev &b = ctx->domain.view;
+  CK(launch_adjoint_fp32(b, ctx->cfg.K, ctx->cfg.s, d, u, nullptr, 0, nullptr,
+                         ctx->pcodes.as<float>(), ctx->stream));
+  CK(launch_synth_fp32(b, ctx->cfg.K, ctx->cfg.s, d, ctx->pcodes.as<float>(), nullptr, nullptr, w,
+                       ctx->stream));
+  return SCSC_OK;
+}
+
+// G = sum over the batch of Z^T r (filter gradient), FP64 [K*M] into gsum.
+scsc_status filter_gradient(scsc_ctx *ctx, const float *r, const float *z, const uint32_t *bits) {
+  const BatchDev &b = ctx->batch.view;
+  const int K = ctx->cfg.K, M = M_of(ctx);
+  CK(ctx->gpart.ensure((size_t)kGradGroups * K * M * 4));
+  CK(ctx->gsum.ensure((size_t)K * M * 8));
+  CK(launch_filter_grad_fp32(b, K, ctx->cfg.s, r, z, bits, ctx->gpart.as<float>(), kGradGroups,
+                             ctx->stream));
+  CK(launch_reduce_partials(ctx->gpart.as<float>(), kGradGroups, K * M, ctx->gsum.as<double>(),
+                            ctx->stream));
+  return SCSC_OK;
+}
+
+// Operator sum_n Z_n^T Z_n on filter space: v -> w (float), via synthesis
+// with filters v and the filter gradient of the result.
+scsc_status apply_ztz(scsc_ctx *ctx, const float *z, const float *v, float *w);
+
+// Generic power iteration on a float vector of length n; writes
+// L = 1.01 * <u, A u> to scal[slot] and, if prm != null, the step params.
+template <typename Op>
+scsc_status power_iteration(scsc_ctx *ctx, int64_t n, uint64_t tag, Op &&apply, int slot,
+                            StepParams *prm, double fixed_step) {
+  CK(ctx->pu.ensure((size_t)n * 4));
+  CK(ctx->pw.ensure((size_t)n * 4));
+  CK(ctx->partials.ensure((size_t)2 * kRedBlocks * 8));
+  CK(ctx->scal.ensure(8 * 8));
+  float *u = ctx->pu.as<float>(), *w = ctx->pw.as<float>();
+  double *part = ctx->partials.as<double>();
+  cudaStream_t st = ctx->stream;
+  CK(launch_power_init(u, n, ctx->cfg.seed, tag, st));
+  CK(launch_dot_partials(u, u, n, part, kRedBlocks, st));
+  CK(launch_power_normalize(u, u, n, part, kRedBlocks, st));
+  for (int it = 0; it < kPowerIters; ++it) {
+    CKS(apply(u, w));
+    CK(launch_dot_partials(w, w, n, part, kRedBlocks, st));
+    CK(launch_power_normalize(w, u, n, part, kRedBlocks, st));
+  }
+  CKS(apply(u, w));
+  CK(launch_dot_partials(u, w, n, part, kRedBlocks, st));
+  CK(launch_power_finish(part, kRedBlocks, kSafety, ctx->scal.as<double>() + slot,
+                         ctx->cfg.lambda, fixed_step, prm, st));
+  return SCSC_OK;
+}
+
+scsc_status apply_ztz(scsc_ctx *ctx, const float *z, const float *v, float *w) {
+  const BatchDev &b = ctx->batch.view;
+  const int K = ctx->cfg.K, M = M_of(ctx);
+  CK(launch_synth_fp32(b, K, ctx->cfg.s, v, z, nullptr, nullptr, ctx->pix2.as<float>(),
+                       ctx->stream));
+  CKS(filter_gradient(ctx, ctx->pix2.as<float>(), z, nullptr));
+  CK(launch_double_to_float(ctx->gsum.as<double>(), w, K * M, ctx->stream));
+  return SCSC_OK;
+}
+
+// Step size of the code update into ctx->prm (device).
+scsc_status code_step_size(scsc_ctx *ctx, const float *d) {
+  CK(ctx->prm.ensure(sizeof(StepParams)));
+  CK(ctx->scal.ensure(8 * 8));
+  StepParams *prm = ctx->prm.as<StepParams>();
+  if (ctx->cfg.step > 0.0) {
+    CK(launch_set_step(prm, ctx->cfg.step, ctx->cfg.lambda, ctx->stream));
+    return SCSC_OK;
+  }
+  int H = ctx->batch.maxH, W = ctx->batch.maxW;
+  if (H != ctx->domainH || W != ctx->domainW) {
+    int64_t zero = 0, id = 0;
+    CKS(upload_batch(ctx, ctx->domain, 1, &zero, &H, &W, &id));
+    ctx->domainH = H;
+    ctx->domainW = W;
+  }
+  CK(ctx->pcodes.ensure((size_t)H * W * ctx->cfg.K * 4));
+  int pr = ctx->prof.begin(KID_POWER, ctx->stream);
+  scsc_status s = power_iteration(
+      ctx, (int64_t)H * W, kTagLz, [&](const float *u, float *w) { return apply_ddt(ctx, d, u, w); },
+      0, prm, 0.0);
+  ctx->prof.end(pr, ctx->stream);
+  return s;
+}
+
+scsc_status check_cfg(scsc_ctx *ctx, const scsc_config *c) {
+  if (!c) return fail(ctx, SCSC_EINVAL, "config is NULL");
+  if (c->K < 1 || c->K > kMaxK) return fail(ctx, SCSC_EINVAL, "K = %d outside [1, %d]", c->K, kMaxK);
+  if (c->s < 1 || c->s > kMaxS || c->s % 2 == 0)
+    return fail(ctx, SCSC_EINVAL, "s = %d must be odd and in [1, %d]", c->s, kMaxS);
+  if (!(c->lambda > 0.0) || !std::isfinite(c->lambda))
+    return fail(ctx, SCSC_EINVAL, "lambda must be finite and > 0");
+  if (c->p_den == 0 || c->p_num > c->p_den)
+    return fail(ctx, SCSC_EINVAL, "p = %u/%u must satisfy 0 <= p <= 1", c->p_num, c->p_den);
+  if (!(c->step >= 0.0) || !std::isfinite(c->step))
+    return fail(ctx, SCSC_EINVAL, "step must be finite and >= 0");
+  if (c->prec != SCSC_FP32 && c->prec != SCSC_BF16)
+    return fail(ctx, SCSC_EINVAL, "unknown precision %d", (int)c->prec);
+  return SCSC_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+extern "C" {
+
+scsc_status scsc_create(const scsc_config *cfg, void *cuda_stream, scsc_ctx **out) {
+  if (!out) return SCSC_EINVAL;
+  *out = nullptr;
+  scsc_ctx tmp;
+  scsc_ctx *ctx = &tmp;
+  CKS(check_cfg(ctx, cfg));
+  scsc_ctx *c = new (std::nothrow) scsc_ctx();
+  if (!c) return SCSC_ENOMEM;
+  c->cfg = *cfg;
+  c->tc.prof = &c->prof;
+  c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return SCSC_ECUDA;
+  }
+  *out = c;
+  return SCSC_OK;
+}
+
+scsc_status scsc_destroy(scsc_ctx *ctx) {
+  if (!ctx) return SCSC_OK;
+  cudaStreamSynchronize(ctx->stream);
+  for (DevBuf *b : {&ctx->bits, &ctx->r, &ctx->pix2, &ctx->prm, &ctx->scal, &ctx->partials,
+                    &ctx->gpart, &ctx->gsum, &ctx->pu, &ctx->pw, &ctx->pcodes, &ctx->flag,
+                    &ctx->C, &ctx->B, &ctx->Cd, &ctx->batch.dev, &ctx->domain.dev})
+    b->release();
+  for (BatchCache *bc : {&ctx->batch, &ctx->domain}) {
+    if (bc->pinned) cudaFreeHost(bc->pinned);
+    if (bc->copied) cudaEventDestroy(bc->copied);
+  }
+  tc_release(ctx->tc);
+  ctx->prof.release();
+  delete ctx;
+  return SCSC_OK;
+}
+
+const char *scsc_last_error(const scsc_ctx *ctx) { return ctx ? ctx->err.c_str() : "NULL context"; }
+
+scsc_status scsc_mask(scsc_ctx *ctx, const scsc_batch *batch, uint64_t t, uint32_t *bits_dev) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!bits_dev) return fail(ctx, SCSC_EINVAL, "bits_dev is NULL");
+  CKS(stage_batch(ctx, batch));
+  const BatchDev &b = ctx->batch.view;
+  CK(launch_mask_bits(b, ctx->cfg.K, ctx->cfg.seed, t, threshold_T(ctx->cfg), bits_dev,
+                      ctx->stream));
+  return SCSC_OK;
+}
+
+scsc_status scsc_lipschitz_codes(scsc_ctx *ctx, const scsc_batch *batch, const float *d_dev,
+                                 double *out_host) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!d_dev || !out_host) return fail(ctx, SCSC_EINVAL, "NULL pointer");
+  CKS(stage_batch(ctx, batch));
+  scsc_config saved = ctx->cfg;
+  ctx->cfg.step = 0.0;  // always run the power iteration here
+  scsc_status s = code_step_size(ctx, d_dev);
+  ctx->cfg = saved;
+  if (s != SCSC_OK) return s;
+  CK(cudaMemcpyAsync(out_host, ctx->scal.as<double>(), 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SCSC_OK;
+}
+
+scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                           const float *d_dev, float *z_dev, uint64_t t, int n_iters) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!x_dev || !d_dev || !z_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
+  if (n_iters < 0) return fail(ctx, SCSC_EINVAL, "n_iters = %d < 0", n_iters);
+  CKS(stage_batch(ctx, batch));
+  const BatchDev &b = ctx->batch.view;
+  const int K = ctx->cfg.K, s = ctx->cfg.s;
+  cudaStream_t st = ctx->stream;
+  CKS(build_mask(ctx, t));
+  CKS(code_step_size(ctx, d_dev));
+  const StepParams *prm = ctx->prm.as<StepParams>();
+  if (ctx->cfg.prec == SCSC_BF16) {
+    int *errw = tc_error_word(ctx->tc);
+    if (!errw) return fail(ctx, SCSC_ENOMEM, "tensor path: error word allocation failed");
+    CK(cudaMemsetAsync(errw, 0, sizeof(int), st));
+    cudaError_t e = tc_code_step(ctx->tc, b, batch->H, batch->W, K, s, x_dev, d_dev, z_dev,
+                                 ctx->bits.as<uint32_t>(), prm, n_iters, st);
+    if (e == cudaErrorNotSupported)
+      return fail(ctx, SCSC_EUNSUPPORTED, "tensor path: %s", tc_last_error(ctx->tc));
+    if (e == cudaErrorTimeout)
+      return fail(ctx, SCSC_ETIMEOUT, "tensor path: a bounded wait ran out (%s)",
+                  tc_last_error(ctx->tc));
+    CK(e);
+    return SCSC_OK;
+  }
+  // Plain FP32 path.  Eq. 4 warm start: unsampled codes are zero.
+  CK(launch_apply_mask_dense(b, K, ctx->bits.as<uint32_t>(), z_dev, st));
+  CK(ctx->r.ensure((size_t)b.total_px * 4));
+  for (int it = 0; it < n_iters; ++it) {
+    int p1 = ctx->prof.begin(KID_SYNTH_FP32, st);
+    CK(launch_synth_fp32(b, K, s, d_dev, z_dev, nullptr, x_dev, ctx->r.as<float>(), st));
+    ctx->prof.end(p1, st);
+    int p2 = ctx->prof.begin(KID_ADJ_FP32, st);
+    CK(launch_adjoint_fp32(b, K, s, d_dev, ctx->r.as<float>(), ctx->bits.as<uint32_t>(), 1, prm,
+                           z_dev, st));
+    ctx->prof.end(p2, st);
+  }
+  return SCSC_OK;
+}
+
+scsc_status scsc_objective(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                           const float *z_dev, const float *d_dev, double *out_host) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!x_dev || !z_dev || !d_dev || !out_host) return fail(ctx, SCSC_EINVAL, "NULL pointer");
+  CKS(stage_batch(ctx, batch));
+  const BatchDev &b = ctx->batch.view;
+  cudaStream_t st = ctx->stream;
+  CK(ctx->r.ensure((size_t)b.total_px * 4));
+  CK(ctx->partials.ensure((size_t)2 * kRedBlocks * 8));
+  CK(ctx->scal.ensure(8 * 8));
+  CK(launch_synth_fp32(b, ctx->cfg.K, ctx->cfg.s, d_dev, z_dev, nullptr, x_dev, ctx->r.as<float>(),
+                       st));
+  CK(launch_sum_sq_abs(ctx->r.as<float>(), b.total_px, z_dev, b.total_px * ctx->cfg.K,
+                       ctx->partials.as<double>(), kRedBlocks, st));
+  CK(launch_finish_sum(ctx->partials.as<double>(), kRedBlocks, 0.5, ctx->cfg.lambda,
+                       ctx->scal.as<double>() + 4, st));
+  CK(cudaMemcpyAsync(out_host, ctx->scal.as<double>() + 4, 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return SCSC_OK;
+}
+
+scsc_status scsc_synth(scsc_ctx *ctx, const scsc_batch *batch, const float *z_dev,
+                       const float *d_dev, uint64_t t, int masked, float *xhat_dev) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!z_dev || !d_dev || !xhat_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
+  CKS(stage_batch(ctx, batch));
+  const uint32_t *bits = nullptr;
+  if (masked) {
+    CKS(build_mask(ctx, t));
+    bits = ctx->bits.as<uint32_t>();
+  }
+  CK(launch_synth_fp32(ctx->batch.view, ctx->cfg.K, ctx->cfg.s, d_dev, z_dev, bits, nullptr,
+                       xhat_dev, ctx->stream));
+  return SCSC_OK;
+}
+
+scsc_status scsc_synth_backward(scsc_ctx *ctx, const scsc_batch *batch, const float *grad_dev,
+                                const float *z_dev, const float *d_dev, uint64_t t, int masked,
+                                float *grad_z_dev, float *grad_d_dev) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!grad_dev || !d_dev || (grad_d_dev && !z_dev))
+    return fail(ctx, SCSC_EINVAL, "NULL device pointer");
+  CKS(stage_batch(ctx, batch));
+  const uint32_t *bits = nullptr;
+  if (masked) {
+    CKS(build_mask(ctx, t));
+    bits = ctx->bits.as<uint32_t>();
+  }
+  const BatchDev &b = ctx->batch.view;
+  if (grad_z_dev)
+    CK(launch_adjoint_fp32(b, ctx->cfg.K, ctx->cfg.s, d_dev, grad_dev, bits, 0, nullptr,
+                           grad_z_dev, ctx->stream));
+  if (grad_d_dev) {
+    CKS(filter_gradient(ctx, grad_dev, z_dev, bits));
+    CK(launch_double_to_float(ctx->gsum.as<double>(), grad_d_dev, ctx->cfg.K * M_of(ctx),
+                              ctx->stream));
+  }
+  return SCSC_OK;
+}
+
+scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                           const float *z_dev, float *d_dev, scsc_dict_mode mode, uint64_t t) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!x_dev || !z_dev || !d_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
+  if (mode != SCSC_DICT_BATCH && mode != SCSC_DICT_ONLINE)
+    return fail(ctx, SCSC_EINVAL, "unknown dictionary mode %d", (int)mode);
+  CKS(stage_batch(ctx, batch));
+  const BatchDev &b = ctx->batch.view;
+  const int K = ctx->cfg.K, s = ctx->cfg.s, M = M_of(ctx);
+  cudaStream_t st = ctx->stream;
+  CK(ctx->scal.ensure(8 * 8));
+  if (mode == SCSC_DICT_BATCH) {
+    CK(ctx->r.ensure((size_t)b.total_px * 4));
+    CK(ctx->pix2.ensure((size_t)b.total_px * 4));
+    CK(ctx->gsum.ensure((size_t)K * M * 8));
+    CK(ctx->Cd.ensure((size_t)K * M * 8));
+    // r = D z - x, G = Z^T r (kept aside while the power iteration reuses gsum)
+    CK(launch_synth_fp32(b, K, s, d_dev, z_dev, nullptr, x_dev, ctx->r.as<float>(), st));
+    CKS(filter_gradient(ctx, ctx->r.as<float>(), z_dev, nullptr));
+    CK(cudaMemcpyAsync(ctx->Cd.p, ctx->gsum.p, (size_t)K * M * 8, cudaMemcpyDeviceToDevice, st));
+    CKS(power_iteration(ctx, (int64_t)K * M, kTagLd,
+                        [&](const float *u, float *w) { return apply_ztz(ctx, z_dev, u, w); }, 1,
+                        nullptr, 0.0));
+    CK(launch_project_step(d_dev, nullptr, ctx->Cd.as<double>(), ctx->scal.as<double>() + 1, K, M,
+                           st));
+    return SCSC_OK;
+  }
+  // Online (Eq. 7, Eq. 8)
+  if (t < 1) return fail(ctx, SCSC_EINVAL, "online dictionary step needs t >= 1");
+  if (t != ctx->online_t + 1)
+    return fail(ctx, SCSC_EINVAL, "online step t = %llu does not follow the state's t = %llu",
+                (unsigned long long)t, (unsigned long long)ctx->online_t);
+  const int64_t KM = (int64_t)K * M;
+  CK(ctx->C.ensure((size_t)KM * KM * 4));
+  CK(ctx->B.ensure((size_t)KM * 8));
+  CK(ctx->Cd.ensure((size_t)KM * 8));
+  if (ctx->online_t == 0) {
+    CK(cudaMemsetAsync(ctx->C.p, 0, (size_t)KM * KM * 4, st));
+    CK(cudaMemsetAsync(ctx->B.p, 0, (size_t)KM * 8, st));
+  }
+  cudaError_t e = launch_surrogate_update(b, K, s, z_dev, x_dev, (double)(t - 1) / (double)t,
+                                          1.0 / ((double)t * b.n), ctx->C.as<float>(),
+                                          ctx->B.as<double>(), st);
+  CK(e);
+  CKS(power_iteration(ctx, KM, kTagLc,
+                      [&](const float *u, float *w) -> scsc_status {
+                        CK(launch_symv(ctx->C.as<float>(), KM, u, nullptr, w, ctx->stream));
+                        return SCSC_OK;
+                      },
+                      2, nullptr, 0.0));
+  // grad = C d - B (FP64 accumulation), then the projected step
+  CK(launch_symv_grad(ctx->C.as<float>(), KM, d_dev, ctx->B.as<double>(), ctx->Cd.as<double>(), st));
+  CK(launch_project_step(d_dev, nullptr, ctx->Cd.as<double>(), ctx->scal.as<double>() + 2, K, M, st));
+  ctx->online_t = t;
+  return SCSC_OK;
+}
+
+scsc_status scsc_sync(scsc_ctx *ctx) {
+  if (!ctx) return SCSC_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ctx->tc.err.p) {
+    int word = 0;
+    CK(cudaMemcpy(&word, ctx->tc.err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (word != 0)
+      return fail(ctx, SCSC_ETIMEOUT, "a tensor-core kernel's bounded wait ran out");
+  }
+  return SCSC_OK;
+}
+
+scsc_status scsc_diag_profile(scsc_ctx *ctx, int enable) {
+  if (!ctx) return SCSC_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof.reset();
+  ctx->prof.on = enable != 0;
+  ctx->tc.prof = &ctx->prof;
+  return SCSC_OK;
+}
+
+scsc_status scsc_diag_kernel_time(scsc_ctx *ctx, const char *name, double *total_ms,
+                                  int *launches) {
+  if (!ctx || !name || !total_ms || !launches) return SCSC_EINVAL;
+  int id = kernel_id(name);
+  if (id < 0) return fail(ctx, SCSC_EINVAL, "unknown kernel name '%s'", name);
+  *total_ms = ctx->prof.total_ms(id, launches);
+  return SCSC_OK;
+}
+
+scsc_status scsc_diag_tc_gemm(int N, const float *A_dev, const float *B_dev, float *D_dev) {
+  int *err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return SCSC_ENOMEM;
+  scsc_status s = SCSC_OK;
+  if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
+      tc_selftest_gemm(N, A_dev, B_dev, D_dev, err, nullptr) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    s = SCSC_ECUDA;
+  } else {
+    int word = 0;
+    if (cudaMemcpy(&word, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) s = SCSC_ECUDA;
+    else if (word) s = SCSC_ETIMEOUT;
+  }
+  cudaFree(err);
+  return s;
+}
+
+scsc_status scsc_online_reset(scsc_ctx *ctx) {
+  if (!ctx) return SCSC_EINVAL;
+  ctx->online_t = 0;
+  return SCSC_OK;
+}
+
+scsc_status scsc_online_state_size(scsc_ctx *ctx, size_t *bytes) {
+  if (!ctx || !bytes) return SCSC_EINVAL;
+  size_t KM = (size_t)ctx->cfg.K * M_of(ctx);
+  *bytes = 4 * 4 + 8 + KM * KM * 4 + KM * 8;
+  return SCSC_OK;
+}
+
+scsc_status scsc_online_save(scsc_ctx *ctx, void *host_buf, size_t bytes) {
+  if (!ctx) return SCSC_EINVAL;
+  size_t need;
+  scsc_online_state_size(ctx, &need);
+  if (!host_buf || bytes < need) return fail(ctx, SCSC_EINVAL, "state buffer needs %zu bytes", need);
+  size_t KM = (size_t)ctx->cfg.K * M_of(ctx);
+  unsigned char *q = static_cast<unsigned char *>(host_buf);
+  uint32_t hdr[4] = {kStateMagic, (uint32_t)ctx->cfg.K, (uint32_t)ctx->cfg.s, 0};
+  memcpy(q, hdr, 16);
+  memcpy(q + 16, &ctx->online_t, 8);
+  if (ctx->online_t == 0) {
+    memset(q + 24, 0, KM * KM * 4 + KM * 8);
+    return SCSC_OK;
+  }
+  CK(cudaMemcpyAsync(q + 24, ctx->C.p, KM * KM * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(q + 24 + KM * KM * 4, ctx->B.p, KM * 8, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return SCSC_OK;
+}
+
+scsc_status scsc_online_load(scsc_ctx *ctx, const void *host_buf, size_t bytes) {
+  if (!ctx) return SCSC_EINVAL;
+  size_t need;
+  scsc_online_state_size(ctx, &need);
+  if (!host_buf || bytes < need) return fail(ctx, SCSC_EINVAL, "state buffer needs %zu bytes", need);
+  const unsigned char *q = static_cast<const unsigned char *>(host_buf);
+  uint32_t hdr[4];
+  memcpy(hdr, q, 16);
+  if (hdr[0] != kStateMagic || (int)hdr[1] != ctx->cfg.K || (int)hdr[2] != ctx->cfg.s)
+    return fail(ctx, SCSC_EINVAL, "state was saved for another K or s");
+  uint64_t t;
+  memcpy(&t, q + 16, 8);
+  size_t KM = (size_t)ctx->cfg.K * M_of(ctx);
+  CK(ctx->C.ensure(KM * KM * 4));
+  CK(ctx->B.ensure(KM * 8));
+  CK(cudaMemcpyAsync(ctx->C.p, q + 24, KM * KM * 4, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->B.p, q + 24 + KM * KM * 4, KM * 8, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->online_t = t;
+  return SCSC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// scsc_internal.cuh -- declarations shared by the CUDA translation units of
+// the SCSC library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace scsc {
+
+constexpr int kMaxK = 512;
+constexpr int kMaxS = 11;
+
+// Device-side view of a batch of images packed back to back.
+struct BatchDev {
+  int n;                // number of images
+  const int64_t *off;   // [n + 1] pixel offsets; off[n] = total pixels
+  const int *H;         // [n]
+  const int *W;         // [n]
+  const int64_t *ids;   // [n] global image index (subsampling hash key)
+  const int *tile0;     // [n + 1] first 32x32 tile of each image
+  int64_t total_px;
+  int n_tiles;          // tile0[n]
+};
+
+// Parameters of the proximal step, read by the kernels from device memory so
+// that the step size computed on the device never round-trips to the host.
+struct StepParams {
+  float alpha;      // step 1/L
+  float thresh;     // alpha * lambda
+};
+
+// ---------------------------------------------------------------- hashing
+
+// SplitMix64 output function (Steele, Lea & Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t splitmix64(uint64_t v) {
+  uint64_t z = v + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Hash prefix shared by every coordinate of image `n` at outer iteration t.
+__host__ __device__ __forceinline__ uint64_t mask_prefix(uint64_t seed, uint64_t t, uint64_t n) {
+  return splitmix64(splitmix64(splitmix64(seed) ^ t) ^ n);
+}
+
+// Largest i in [0, n) with start[i] <= g (start ascending, start[0] = 0).
+template <typename T>
+__device__ __forceinline__ int upper_index(const T *start, int n, int64_t g) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if ((int64_t)start[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float soft_threshold(float v, float tau) {
+  // sign(v) max(|v| - tau, 0); |v| <= tau gives exactly 0
+  return v > tau ? v - tau : (v < -tau ? v + tau : 0.0f);
+}
+
+}  // namespace scsc
+
+// ---------------------------------------------------------------- launchers
+// Every launcher enqueues on `st` and returns the launch status.
+namespace scsc {
+
+cudaError_t launch_mask_bits(const BatchDev &b, int K, uint64_t seed, uint64_t t, uint64_t T,
+                             uint32_t *bits, cudaStream_t st);
+cudaError_t launch_apply_mask_dense(const BatchDev &b, int K, const uint32_t *bits, float *z,
+                                    cudaStream_t st);
+cudaError_t launch_synth_fp32(const BatchDev &b, int K, int s, const float *d, const float *z,
+                              const uint32_t *bits, const float *x, float *out, cudaStream_t st);
+cudaError_t launch_adjoint_fp32(const BatchDev &b, int K, int s, const float *d, const float *r,
+                                const uint32_t *bits, int mode, const StepParams *prm,
+                                float *z_or_g, cudaStream_t st);
+cudaError_t launch_filter_grad_fp32(const BatchDev &b, int K, int s, const float *r,
+                                    const float *z, const uint32_t *bits, float *partial,
+                                    int n_groups, cudaStream_t st);
+cudaError_t launch_reduce_partials(const float *partial, int n_groups, int len, double *out,
+                                   cudaStream_t st);
+cudaError_t launch_sum_sq_abs(const float *a, int64_t n_sq, const float *b, int64_t n_abs,
+                              double *partials, int n_blocks, cudaStream_t st);
+cudaError_t launch_finish_sum(const double *partials, int n_blocks, double scale_sq,
+                              double scale_abs, double *out, cudaStream_t st);
+cudaError_t launch_power_init(float *u, int64_t n, uint64_t seed, uint64_t tag, cudaStream_t st);
+cudaError_t launch_dot_partials(const float *a, const float *b, int64_t n, double *partials,
+                                int n_blocks, cudaStream_t st);
+cudaError_t launch_power_normalize(const float *w, float *u, int64_t n, const double *partials,
+                                   int n_blocks, cudaStream_t st);
+cudaError_t launch_power_finish(const double *partials, int n_blocks, double safety,
+                                double *L_out, double lambda, double fixed_step,
+                                StepParams *prm, cudaStream_t st);
+cudaError_t launch_project_step(float *d, const float *G_or_null, const double *Gd_or_null,
+                                const double *L, int K, int M, cudaStream_t st);
+cudaError_t launch_check_finite(const float *a, int64_t n, int *flag, cudaStream_t st);
+
+}  // namespace scsc

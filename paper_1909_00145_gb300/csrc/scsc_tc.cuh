@@ -1,0 +1,57 @@
+// scsc_tc.cuh -- the tensor-core (tcgen05, BF16 operands, FP32 accumulation)
+// code-update path and the small helpers shared with the plain path.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "profiler.cuh"
+#include "scsc_internal.cuh"
+
+namespace scsc {
+
+// Workspace of the tensor path, owned by the context.
+struct TcWorkspace {
+  struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+  };
+  Buf item0, seg_count, seg_base, scan_blocks, packed, xcore, spill, r, badj, bsyn, err;
+  std::vector<int> host_item0;  // cached row-item map of the last batch
+  std::vector<int> host_H, host_W;
+  int n_items = 0;
+  int sm_count = 0;
+  Profiler *prof = nullptr;  // the owning context's profiler
+  std::string last_error;
+};
+
+// One outer iteration of the code update on the tensor path (see
+// scsc_code_step): pack the warm start on the sampled set, n_iters
+// proximal-gradient iterations on packed FP32 codes with BF16 tcgen05
+// synthesis and adjoint, unpack to dense codes (Eq. 4).
+// H_host / W_host are the batch's host arrays (n images).
+cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, const int *W_host,
+                         int K, int s, const float *x, const float *d, float *z,
+                         const uint32_t *bits, const StepParams *prm, int n_iters,
+                         cudaStream_t st);
+// Device error word of the tensor kernels (0 = ok, 1 = bounded wait ran out).
+int *tc_error_word(TcWorkspace &ws);
+void tc_release(TcWorkspace &ws);
+const char *tc_last_error(const TcWorkspace &ws);
+
+// D[128 x N] = A[128 x 64] * B[N x 64]^T through one tcgen05 pipeline (BF16
+// operands rounded from the float inputs, FP32 accumulation); device buffers.
+cudaError_t tc_selftest_gemm(int N, const float *A, const float *B, float *D, int *err,
+                             cudaStream_t st);
+
+// Helpers implemented in kernels_online.cu.
+cudaError_t launch_surrogate_update(const BatchDev &b, int K, int s, const float *z, const float *x,
+                                    double alpha, double beta, float *Cm, double *Bv,
+                                    cudaStream_t st);
+cudaError_t launch_symv(const float *Cm, int64_t n, const float *v, const double *unused,
+                        float *out, cudaStream_t st);
+cudaError_t launch_symv_grad(const float *Cm, int64_t n, const float *d, const double *Bv,
+                             double *out, cudaStream_t st);
+cudaError_t launch_double_to_float(const double *in, float *out, int n, cudaStream_t st);
+cudaError_t launch_set_step(StepParams *prm, double step, double lambda, cudaStream_t st);
+
+}  // namespace scsc

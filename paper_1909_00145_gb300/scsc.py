@@ -1,0 +1,322 @@
+"""ctypes binding of the SCSC C ABI (include/scsc.h).
+
+Argument marshalling only: every step runs in the CUDA library.  Functions
+carry the names of the C entry points; :class:`Context` and :class:`Batch`
+hold the handle and the host descriptor arrays.  Tensors are torch CUDA
+float32 tensors (contiguous); torch supplies device memory and streams.
+The library is loaded on first use; if it is missing and cannot be built,
+the call raises -- there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+c_int, c_double, c_u32, c_u64, c_i64, c_void_p, c_size_t = (
+    ctypes.c_int, ctypes.c_double, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64,
+    ctypes.c_void_p, ctypes.c_size_t)
+
+SCSC_OK, SCSC_EINVAL, SCSC_ENOMEM, SCSC_ECUDA, SCSC_ETIMEOUT, SCSC_ENONFINITE, SCSC_EUNSUPPORTED = range(7)
+STATUS_NAMES = ["SCSC_OK", "SCSC_EINVAL", "SCSC_ENOMEM", "SCSC_ECUDA", "SCSC_ETIMEOUT",
+                "SCSC_ENONFINITE", "SCSC_EUNSUPPORTED"]
+SCSC_FP32, SCSC_BF16 = 0, 1
+SCSC_DICT_BATCH, SCSC_DICT_ONLINE = 0, 1
+
+
+class scsc_config(ctypes.Structure):
+    _fields_ = [("K", c_int), ("s", c_int), ("lambda_", c_double), ("p_num", c_u32),
+                ("p_den", c_u32), ("seed", c_u64), ("prec", c_int), ("step", c_double)]
+
+
+class scsc_batch(ctypes.Structure):
+    _fields_ = [("n_images", c_int), ("offsets", ctypes.POINTER(c_i64)),
+                ("H", ctypes.POINTER(c_int)), ("W", ctypes.POINTER(c_int)),
+                ("image_ids", ctypes.POINTER(c_i64))]
+
+
+class ScscError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+_SIGNATURES = {
+    "scsc_create": [ctypes.POINTER(scsc_config), c_void_p, ctypes.POINTER(c_void_p)],
+    "scsc_destroy": [c_void_p],
+    "scsc_mask": [c_void_p, ctypes.POINTER(scsc_batch), c_u64, c_void_p],
+    "scsc_code_step": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p, c_u64,
+                       c_int],
+    "scsc_dict_step": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p, c_int,
+                       c_u64],
+    "scsc_objective": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p,
+                       ctypes.POINTER(c_double)],
+    "scsc_lipschitz_codes": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p,
+                             ctypes.POINTER(c_double)],
+    "scsc_synth": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_u64, c_int,
+                   c_void_p],
+    "scsc_synth_backward": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p,
+                            c_u64, c_int, c_void_p, c_void_p],
+    "scsc_sync": [c_void_p],
+    "scsc_online_reset": [c_void_p],
+    "scsc_online_state_size": [c_void_p, ctypes.POINTER(c_size_t)],
+    "scsc_online_save": [c_void_p, c_void_p, c_size_t],
+    "scsc_online_load": [c_void_p, c_void_p, c_size_t],
+    "scsc_diag_tc_gemm": [c_int, c_void_p, c_void_p, c_void_p],
+    "scsc_diag_profile": [c_void_p, c_int],
+    "scsc_diag_kernel_time": [c_void_p, ctypes.c_char_p, ctypes.POINTER(c_double),
+                              ctypes.POINTER(c_int)],
+}
+
+
+def lib() -> ctypes.CDLL:
+    """Load the in-tree CUDA library, building it first if it is stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, args in _SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = c_int
+            L.scsc_last_error.argtypes = [c_void_p]
+            L.scsc_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(status: int, handle=None, what: str = "") -> None:
+    if status != SCSC_OK:
+        msg = what
+        if handle:
+            m = lib().scsc_last_error(handle)
+            if m:
+                msg = f"{what}: {m.decode()}" if what else m.decode()
+        raise ScscError(status, msg)
+
+
+def _ptr(t) -> int:
+    """Device pointer of a contiguous CUDA float32/uint32 tensor (0 for None)."""
+    if t is None:
+        return 0
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+class Batch:
+    """Host descriptor of images packed back to back (scsc_batch)."""
+
+    def __init__(self, H, W, ids=None):
+        self.H = np.ascontiguousarray(np.atleast_1d(H), dtype=np.int32)
+        self.W = np.ascontiguousarray(np.atleast_1d(W), dtype=np.int32)
+        if self.H.shape != self.W.shape:
+            raise ValueError("H and W must have the same length")
+        n = len(self.H)
+        self.ids = np.ascontiguousarray(np.arange(n) if ids is None else ids, dtype=np.int64)
+        sizes = self.H.astype(np.int64) * self.W.astype(np.int64)
+        self.offsets = np.ascontiguousarray(
+            np.concatenate([[0], np.cumsum(sizes)[:-1]]), dtype=np.int64)
+        self.total_pixels = int(sizes.sum())
+        self.c = scsc_batch(n, self.offsets.ctypes.data_as(ctypes.POINTER(c_i64)),
+                            self.H.ctypes.data_as(ctypes.POINTER(c_int)),
+                            self.W.ctypes.data_as(ctypes.POINTER(c_int)),
+                            self.ids.ctypes.data_as(ctypes.POINTER(c_i64)))
+
+    @property
+    def n(self) -> int:
+        return len(self.H)
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Context:
+    """An scsc_ctx bound to the current device and a CUDA stream."""
+
+    def __init__(self, K: int, s: int = 11, lam: float = 1.0, p=(1, 1), seed: int = 0,
+                 prec: str = "fp32", step: float = 0.0, stream=None):
+        self.K, self.s, self.lam = int(K), int(s), float(lam)
+        self.p = (int(p[0]), int(p[1]))
+        self.seed = int(seed)
+        self.prec = {"fp32": SCSC_FP32, "bf16": SCSC_BF16}[prec]
+        self.cfg = scsc_config(self.K, self.s, self.lam, self.p[0], self.p[1], self.seed,
+                               self.prec, float(step))
+        self.stream = stream
+        self.handle = c_void_p()
+        _check(lib().scsc_create(ctypes.byref(self.cfg), c_void_p(_stream_handle(stream)),
+                                 ctypes.byref(self.handle)), None, "scsc_create")
+
+    def close(self) -> None:
+        if self.handle:
+            lib().scsc_destroy(self.handle)
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # methods mirror the C entry points
+    def code_step(self, batch, x, d, z, t, n_iters):
+        return scsc_code_step(self, batch, x, d, z, t, n_iters)
+
+    def dict_step(self, batch, x, z, d, mode=SCSC_DICT_BATCH, t=1):
+        return scsc_dict_step(self, batch, x, z, d, mode, t)
+
+    def objective(self, batch, x, z, d) -> float:
+        return scsc_objective(self, batch, x, z, d)
+
+    def mask(self, batch, t):
+        return scsc_mask(self, batch, t)
+
+    def lipschitz_codes(self, batch, d) -> float:
+        return scsc_lipschitz_codes(self, batch, d)
+
+    def synth(self, batch, z, d, t=0, masked=False, out=None):
+        return scsc_synth(self, batch, z, d, t, masked, out)
+
+    def synth_backward(self, batch, grad, z, d, t=0, masked=False, need_z=True, need_d=True):
+        return scsc_synth_backward(self, batch, grad, z, d, t, masked, need_z, need_d)
+
+    def sync(self):
+        return scsc_sync(self)
+
+
+# ------------------------------------------------------------------ entry points
+
+def scsc_create(K, s=11, lam=1.0, p=(1, 1), seed=0, prec="fp32", step=0.0, stream=None):
+    return Context(K, s, lam, p, seed, prec, step, stream)
+
+
+def scsc_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def scsc_last_error(ctx: Context) -> str:
+    return lib().scsc_last_error(ctx.handle).decode()
+
+
+def scsc_mask(ctx: Context, batch: Batch, t: int):
+    import torch
+    kw = (ctx.K + 31) // 32
+    bits = torch.empty(batch.total_pixels * kw, dtype=torch.int32, device="cuda")
+    _check(lib().scsc_mask(ctx.handle, ctypes.byref(batch.c), t, _ptr(bits)), ctx.handle,
+           "scsc_mask")
+    return bits
+
+
+def scsc_code_step(ctx: Context, batch: Batch, x, d, z, t: int, n_iters: int) -> None:
+    _check(lib().scsc_code_step(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d), _ptr(z), t,
+                                n_iters), ctx.handle, "scsc_code_step")
+
+
+def scsc_dict_step(ctx: Context, batch: Batch, x, z, d, mode: int = SCSC_DICT_BATCH,
+                   t: int = 1) -> None:
+    _check(lib().scsc_dict_step(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(z), _ptr(d),
+                                mode, t), ctx.handle, "scsc_dict_step")
+
+
+def scsc_objective(ctx: Context, batch: Batch, x, z, d) -> float:
+    out = c_double()
+    _check(lib().scsc_objective(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(z), _ptr(d),
+                                ctypes.byref(out)), ctx.handle, "scsc_objective")
+    return out.value
+
+
+def scsc_lipschitz_codes(ctx: Context, batch: Batch, d) -> float:
+    out = c_double()
+    _check(lib().scsc_lipschitz_codes(ctx.handle, ctypes.byref(batch.c), _ptr(d),
+                                      ctypes.byref(out)), ctx.handle, "scsc_lipschitz_codes")
+    return out.value
+
+
+def scsc_synth(ctx: Context, batch: Batch, z, d, t: int = 0, masked: bool = False, out=None):
+    import torch
+    if out is None:
+        out = torch.empty(batch.total_pixels, dtype=torch.float32, device=z.device)
+    _check(lib().scsc_synth(ctx.handle, ctypes.byref(batch.c), _ptr(z), _ptr(d), t, int(masked),
+                            _ptr(out)), ctx.handle, "scsc_synth")
+    return out
+
+
+def scsc_synth_backward(ctx: Context, batch: Batch, grad, z, d, t: int = 0, masked: bool = False,
+                        need_z: bool = True, need_d: bool = True):
+    import torch
+    gz = torch.empty(batch.total_pixels * ctx.K, dtype=torch.float32, device=grad.device) if need_z else None
+    gd = torch.empty(ctx.K * ctx.s * ctx.s, dtype=torch.float32, device=grad.device) if need_d else None
+    _check(lib().scsc_synth_backward(ctx.handle, ctypes.byref(batch.c), _ptr(grad), _ptr(z),
+                                     _ptr(d), t, int(masked), _ptr(gz), _ptr(gd)), ctx.handle,
+           "scsc_synth_backward")
+    return gz, gd
+
+
+def scsc_sync(ctx: Context) -> None:
+    _check(lib().scsc_sync(ctx.handle), ctx.handle, "scsc_sync")
+
+
+def scsc_online_reset(ctx: Context) -> None:
+    _check(lib().scsc_online_reset(ctx.handle), ctx.handle, "scsc_online_reset")
+
+
+def scsc_online_state_size(ctx: Context) -> int:
+    n = c_size_t()
+    _check(lib().scsc_online_state_size(ctx.handle, ctypes.byref(n)), ctx.handle)
+    return n.value
+
+
+def scsc_online_save(ctx: Context) -> bytearray:
+    n = scsc_online_state_size(ctx)
+    buf = bytearray(n)
+    cbuf = (ctypes.c_char * n).from_buffer(buf)
+    _check(lib().scsc_online_save(ctx.handle, ctypes.addressof(cbuf), n), ctx.handle,
+           "scsc_online_save")
+    return buf
+
+
+def scsc_online_load(ctx: Context, buf) -> None:
+    buf = bytearray(buf)
+    cbuf = (ctypes.c_char * len(buf)).from_buffer(buf)
+    _check(lib().scsc_online_load(ctx.handle, ctypes.addressof(cbuf), len(buf)), ctx.handle,
+           "scsc_online_load")
+
+
+def scsc_diag_tc_gemm(A, B):
+    """tcgen05 self-check: returns D = bf16(A) bf16(B)^T computed on the tensor core."""
+    import torch
+    N = B.shape[0]
+    D = torch.empty((128, N), dtype=torch.float32, device=A.device)
+    _check(lib().scsc_diag_tc_gemm(N, _ptr(A), _ptr(B), _ptr(D)), None, "scsc_diag_tc_gemm")
+    return D
+
+
+def scsc_diag_profile(ctx: Context, enable: bool = True) -> None:
+    _check(lib().scsc_diag_profile(ctx.handle, int(enable)), ctx.handle, "scsc_diag_profile")
+
+
+def scsc_diag_kernel_time(ctx: Context, name: str):
+    """(total device ms, launches) of one library kernel since profiling began."""
+    ms, n = c_double(), c_int()
+    _check(lib().scsc_diag_kernel_time(ctx.handle, name.encode(), ctypes.byref(ms),
+                                       ctypes.byref(n)), ctx.handle, "scsc_diag_kernel_time")
+    return ms.value, n.value

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA library against the FP64 oracle on the same seeded
+inputs.  Masks are compared bit for bit; floating point within the stated
+tolerances (FP32 path: objective 1e-5 rel, codes/filters 1e-4 rel L2; BF16
+path: objective 1e-3 rel)."""
+import numpy as np
+import pytest
+
+from oracle import reference as R
+from tests.helpers import make_case, oracle_bits, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1909_00145_gb300 import scsc  # noqa: E402
+
+
+def dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+# ------------------------------------------------------------------ tcgen05 encodings
+
+@pytest.mark.parametrize("N", [16, 112, 176, 256])
+def test_tcgen05_gemm_selfcheck(N):
+    g = torch.Generator().manual_seed(N)
+    A = torch.randn(128, 64, generator=g)
+    B = torch.randn(N, 64, generator=g)
+    D = scsc.scsc_diag_tc_gemm(A.cuda(), B.cuda()).cpu()
+    ref = A.to(torch.bfloat16).double() @ B.to(torch.bfloat16).double().T
+    assert rel_l2(D.numpy(), ref.numpy()) < 1e-6
+
+
+# ------------------------------------------------------------------ mask
+
+@pytest.mark.parametrize("K,p,H,W", [(16, (1, 2), [100], [100]), (100, (1, 4), [37, 20], [50, 131]),
+                                     (3, (1, 1), [5], [7]), (33, (0, 1), [9], [8]),
+                                     (64, (3, 10), [64, 17], [64, 200])])
+def test_mask_is_bit_exact(K, p, H, W):
+    cfg = R.Config(K=K, p_num=p[0], p_den=p[1], seed=12345)
+    ids = list(range(3, 3 + len(H)))
+    ob = oracle_bits(cfg, R.Batch(H=H, W=W, ids=ids), t=7)
+    ctx = scsc.Context(K, p=p, seed=12345)
+    gb = host(ctx.mask(scsc.Batch(H, W, ids), 7)).view(np.uint32)
+    assert np.array_equal(gb, ob)
+
+
+# ------------------------------------------------------------------ operators
+
+@pytest.mark.parametrize("K,s,H,W,masked", [(16, 11, [100], [100], False), (7, 5, [33, 9], [70, 40], True),
+                                           (100, 11, [40], [45], True), (1, 1, [3], [2], False)])
+def test_synthesis_and_backward_fp32(K, s, H, W, masked):
+    x, d, z = make_case(H, W, K, s, seed=5, code_density=0.2)
+    cfg = R.Config(K=K, s=s, p_num=1, p_den=2, seed=9)
+    rb = R.Batch(H=H, W=W, ids=[0] * len(H) if False else list(range(len(H))))
+    zm = z.copy()
+    if masked:
+        zm = np.where(R.mask_batch(cfg, rb, 4).astype(bool), z, 0).astype(np.float32)
+    ctx = scsc.Context(K, s, p=(1, 2), seed=9)
+    b = scsc.Batch(H, W)
+    zt, dt = dev(z), dev(d)
+    xh = host(ctx.synth(b, zt, dt, t=4, masked=masked))
+    xo = R.synthesis_batch(cfg, rb, zm, d)
+    assert rel_l2(xh, xo) < 1e-5
+    g = np.random.default_rng(1).normal(size=b.total_pixels).astype(np.float32)
+    gz, gd = ctx.synth_backward(b, dev(g), zt, dt, t=4, masked=masked)
+    gz_o = np.concatenate([R.adjoint(d, rb.image(g, n), K, s, int(H[n]), int(W[n]))
+                           for n in range(len(H))])
+    if masked:
+        gz_o = np.where(R.mask_batch(cfg, rb, 4).astype(bool), gz_o, 0)
+    gd_o = sum(R.filter_gradient(rb.image(g, n), rb.image(zm, n, K), K, s, int(H[n]), int(W[n]))
+               for n in range(len(H)))
+    assert rel_l2(host(gz), gz_o) < 1e-5
+    assert rel_l2(host(gd), gd_o) < 1e-5
+
+
+def test_adjoint_identity_on_device():
+    K, s, H, W = 24, 11, [64], [96]
+    x, d, z = make_case(H, W, K, s, seed=2, code_density=0.3)
+    ctx = scsc.Context(K, s)
+    b = scsc.Batch(H, W)
+    r = np.random.default_rng(3).normal(size=b.total_pixels).astype(np.float32)
+    Dz = host(ctx.synth(b, dev(z), dev(d))).astype(np.float64)
+    gz, gd = ctx.synth_backward(b, dev(r), dev(z), dev(d))
+    lhs = np.dot(Dz, r)
+    assert abs(lhs - np.dot(z.astype(np.float64), host(gz))) <= 1e-5 * abs(lhs)
+    assert abs(lhs - np.dot(d.ravel().astype(np.float64), host(gd))) <= 1e-5 * abs(lhs)
+
+
+def test_lipschitz_and_objective_fp32():
+    K, s, H, W = 16, 11, [60, 48], [50, 64]
+    x, d, z = make_case(H, W, K, s, seed=4, code_density=0.1)
+    cfg = R.Config(K=K, s=s, lam=0.7, seed=21)
+    rb = R.Batch(H=H, W=W, ids=[0, 1])
+    ctx = scsc.Context(K, s, lam=0.7, seed=21)
+    b = scsc.Batch(H, W)
+    L = ctx.lipschitz_codes(b, dev(d))
+    assert L == pytest.approx(R.lipschitz_codes(cfg, d, max(H), max(W)), rel=1e-4)
+    f = ctx.objective(b, dev(x), dev(z), dev(d))
+    assert f == pytest.approx(R.objective(cfg, rb, x, z, d), rel=1e-6)
+
+
+# ------------------------------------------------------------------ code step
+
+def run_code_step(prec, K, s, H, W, p, n_iters, t=1, seed=0, lam=1.0, warm=None, step=0.0):
+    x, d, _ = make_case(H, W, K, s, seed=seed)
+    z0 = np.zeros(int(np.sum(np.multiply(H, W))) * K, dtype=np.float32) if warm is None else warm
+    ctx = scsc.Context(K, s, lam=lam, p=p, seed=seed + 100, prec=prec, step=step)
+    b = scsc.Batch(H, W, ids=list(range(10, 10 + len(H))))
+    zt = dev(z0)
+    ctx.code_step(b, dev(x), dev(d), zt, t, n_iters)
+    ctx.sync()
+    cfg = R.Config(K=K, s=s, lam=lam, p_num=p[0], p_den=p[1], seed=seed + 100)
+    rb = R.Batch(H=H, W=W, ids=list(range(10, 10 + len(H))))
+    zo = R.code_step(cfg, rb, x, d, z0, t, n_iters, step=step if step > 0 else None)
+    fo = R.objective(cfg, rb, x, zo, d)
+    fg = ctx.objective(b, dev(x), zt, dev(d))
+    return host(zt), zo, fg, fo, (x, d, cfg, rb)
+
+
+def test_code_step_c1_fp32():
+    """Config C1: one 100x100 image, K=16, p=0.5, lambda=1, 20 iterations."""
+    zg, zo, fg, fo, _ = run_code_step("fp32", 16, 11, [100], [100], (1, 2), 20)
+    assert rel_l2(zg, zo) < 1e-4
+    assert fg == pytest.approx(fo, rel=1e-5)
+
+
+def test_code_step_c1_bf16():
+    zg, zo, fg, fo, _ = run_code_step("bf16", 16, 11, [100], [100], (1, 2), 20)
+    assert fg == pytest.approx(fo, rel=1e-3)
+    assert rel_l2(zg, zo) < 5e-2
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_code_step_ragged_batch(prec):
+    """Uneven sizes: a strip boundary (W > 128), a ragged last strip, narrow
+    and short images; K not a multiple of 16; s = 5."""
+    H, W = [37, 20, 3, 64], [131, 260, 5, 64]
+    zg, zo, fg, fo, _ = run_code_step(prec, 20, 5, H, W, (1, 3), 12, seed=3, lam=0.5)
+    tol = 1e-5 if prec == "fp32" else 1e-3
+    assert fg == pytest.approx(fo, rel=tol)
+    assert rel_l2(zg, zo) < (1e-4 if prec == "fp32" else 5e-2)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_code_step_warm_start_and_p_one(prec):
+    K, s, H, W = 8, 7, [30], [140]
+    x, d, z = make_case(H, W, K, s, seed=8, code_density=0.2)
+    zg, zo, fg, fo, _ = run_code_step(prec, K, s, H, W, (1, 1), 5, t=3, seed=8, lam=0.3, warm=z)
+    assert fg == pytest.approx(fo, rel=1e-5 if prec == "fp32" else 1e-3)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_code_step_p_zero_and_zero_iterations(prec):
+    K, s, H, W = 5, 3, [9], [12]
+    x, d, z = make_case(H, W, K, s, seed=1, code_density=0.5)
+    zg, zo, fg, fo, _ = run_code_step(prec, K, s, H, W, (0, 1), 3, warm=z)
+    assert not zg.any() and not zo.any()
+    zg, zo, fg, fo, _ = run_code_step(prec, K, s, H, W, (1, 2), 0, warm=z, seed=1)
+    assert np.array_equal(zg, zo.astype(np.float32))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_code_step_fixed_step(prec):
+    zg, zo, fg, fo, _ = run_code_step(prec, 12, 11, [40], [150], (1, 4), 8, step=0.02, lam=0.8)
+    assert fg == pytest.approx(fo, rel=1e-5 if prec == "fp32" else 1e-3)
+
+
+# ------------------------------------------------------------------ dictionary steps
+
+def test_dict_step_batch_fp32():
+    K, s, H, W = 12, 11, [40, 33], [50, 61]
+    x, d, z = make_case(H, W, K, s, seed=6, code_density=0.05)
+    cfg = R.Config(K=K, s=s, seed=77)
+    rb = R.Batch(H=H, W=W, ids=[0, 1])
+    do = R.dict_step_batch(cfg, rb, x, z, d)
+    ctx = scsc.Context(K, s, seed=77)
+    b = scsc.Batch(H, W)
+    dt = dev(d)
+    ctx.dict_step(b, dev(x), dev(z), dt, scsc.SCSC_DICT_BATCH, 1)
+    assert rel_l2(host(dt), do) < 1e-4
+    assert np.all(np.linalg.norm(host(dt).reshape(K, -1), axis=1) <= 1 + 1e-6)
+
+
+def test_dict_step_online_fp32_and_state_roundtrip():
+    K, s, H, W = 4, 5, [12, 10], [14, 16]
+    cfg = R.Config(K=K, s=s, seed=5)
+    st = R.OnlineState(cfg)
+    ctx = scsc.Context(K, s, seed=5)
+    b = scsc.Batch(H, W)
+    rb = R.Batch(H=H, W=W, ids=[0, 1])
+    x, d, _ = make_case(H, W, K, s, seed=11)
+    dt = dev(d)
+    d_o = d.astype(np.float64).ravel()
+    saved = None
+    for t in range(1, 4):
+        _, _, z = make_case(H, W, K, s, seed=20 + t, code_density=0.2)
+        st.update(rb, x, z)
+        d_o = st.dict_step(d_o)
+        ctx.dict_step(b, dev(x), dev(z), dt, scsc.SCSC_DICT_ONLINE, t)
+        assert rel_l2(host(dt), d_o) < 1e-4
+        if t == 2:
+            saved = scsc.scsc_online_save(ctx)
+            d_saved = dt.clone()
+    # resume from the saved state reproduces step 3
+    ctx2 = scsc.Context(K, s, seed=5)
+    scsc.scsc_online_load(ctx2, saved)
+    _, _, z = make_case(H, W, K, s, seed=23, code_density=0.2)
+    ctx2.dict_step(b, dev(x), dev(z), d_saved, scsc.SCSC_DICT_ONLINE, 3)
+    assert torch.equal(d_saved, dt)

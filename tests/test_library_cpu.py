@@ -1,0 +1,70 @@
+"""CPU checks of the CUDA library: it builds for sm_103a, loads, exports every
+symbol the public headers declare, and rejects bad arguments on the host."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1909_00145_gb300 import scsc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(scsc_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_headers_declare_the_boundary():
+    names = declared_symbols()
+    for need in ["scsc_create", "scsc_destroy", "scsc_code_step", "scsc_dict_step",
+                 "scsc_objective", "scsc_mask", "scsc_synth", "scsc_synth_backward",
+                 "scsc_lipschitz_codes", "scsc_last_error", "scsc_sync", "scsc_online_save",
+                 "scsc_online_load", "scsc_online_reset", "scsc_online_state_size"]:
+        assert need in names
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    L = scsc.lib()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+
+
+def test_library_is_built_for_sm103a():
+    path = scsc.library_path()
+    data = open(path, "rb").read()
+    assert b"sm_103a" in data or b"sm_103" in data
+
+
+def test_config_validation_happens_on_the_host():
+    L = scsc.lib()
+    bad = [dict(K=0), dict(K=600), dict(s=4), dict(s=13), dict(lam=0.0), dict(p=(3, 2)),
+           dict(p=(1, 0)), dict(step=-1.0)]
+    for kw in bad:
+        args = dict(K=16, s=11, lam=1.0, p=(1, 2), step=0.0)
+        args.update(kw)
+        cfg = scsc.scsc_config(args["K"], args["s"], args["lam"], args["p"][0], args["p"][1], 0,
+                               0, args["step"])
+        h = ctypes.c_void_p()
+        assert L.scsc_create(ctypes.byref(cfg), None, ctypes.byref(h)) == scsc.SCSC_EINVAL, kw
+        assert not h
+
+
+def test_null_context_is_rejected():
+    L = scsc.lib()
+    assert L.scsc_destroy(None) == scsc.SCSC_OK
+    assert L.scsc_sync(None) == scsc.SCSC_EINVAL
+    assert L.scsc_code_step(None, None, None, None, None, 0, 1) == scsc.SCSC_EINVAL
+
+
+def test_batch_descriptor_layout():
+    b = scsc.Batch([3, 5], [4, 2], ids=[7, 9])
+    assert list(b.offsets) == [0, 12]
+    assert b.total_pixels == 22
+    assert ctypes.sizeof(scsc.scsc_config) == 48
