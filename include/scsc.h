@@ -143,6 +143,29 @@ scsc_status scsc_synth_backward(scsc_ctx *ctx, const scsc_batch *batch, const fl
  * remaining work and released its tensor memory). */
 scsc_status scsc_sync(scsc_ctx *ctx);
 
+/* Objective of Eq. 1 for n_images images that all have H x W pixels (packed
+ * back to back; codes [H][W][K] per image), written to *out_dev (one device
+ * double), enqueued on cuda_stream (NULL = legacy default stream).  It
+ * allocates no device memory, so callers that cannot call cudaMalloc can use
+ * it: code inside stream capture, services whose memory pool already holds
+ * the whole device, loops that cannot take an allocation's implicit
+ * synchronisation.  The paper has no counterpart; this is a service of this
+ * library.  Needs no context: cfg supplies K, s and lambda (p, seed, prec and
+ * step are ignored).
+ * Scratch: a fixed array of 65,536 + 1,024 doubles (520 KiB) compiled into
+ * the library, which every GPU that loads the library holds until the
+ * process exits.  The batch may therefore span at most 65,536 tiles of
+ * 32 x 32 pixels (n_images * ceil(H/32) * ceil(W/32) <= 65,536); larger
+ * batches are rejected with SCSC_EINVAL before anything is launched.
+ * The first call on a device looks up the array's device address with that
+ * device current; make that first call outside any stream capture.  All
+ * calls share the array and each call overwrites what it reads, so calls
+ * that overlap on the GPU (on different streams or devices sharing nothing
+ * else) race and must be serialised by the caller. */
+scsc_status scsc_objective_noalloc(const scsc_config *cfg, int n_images, int H, int W,
+                                   const float *x_dev, const float *z_dev, const float *d_dev,
+                                   double *out_dev, void *cuda_stream);
+
 /* Online surrogates (Eq. 7): reset to C = 0, B = 0, t = 0; query the byte
  * size of the serialised state; save to / load from a host buffer
  * (format: magic, K, s, t, then C [KM][KM] float32 and B [KM] float64). */

@@ -71,6 +71,8 @@ _SIGNATURES = {
     "scsc_online_save": [c_void_p, c_void_p, c_size_t],
     "scsc_online_load": [c_void_p, c_void_p, c_size_t],
     "scsc_diag_tc_gemm": [c_int, c_void_p, c_void_p, c_void_p],
+    "scsc_objective_noalloc": [ctypes.POINTER(scsc_config), c_int, c_int, c_int, c_void_p,
+                               c_void_p, c_void_p, c_void_p, c_void_p],
     "scsc_diag_profile": [c_void_p, c_int],
     "scsc_diag_kernel_time": [c_void_p, ctypes.c_char_p, ctypes.POINTER(c_double),
                               ctypes.POINTER(c_int)],
@@ -269,6 +271,16 @@ def scsc_synth_backward(ctx: Context, batch: Batch, grad, z, d, t: int = 0, mask
                                      _ptr(d), t, int(masked), _ptr(gz), _ptr(gd)), ctx.handle,
            "scsc_synth_backward")
     return gz, gd
+
+
+def scsc_objective_noalloc(K: int, s: int, lam: float, n_images: int, H: int, W: int, x, z, d,
+                           out, stream=None) -> None:
+    """Eq. 1 for equal-size images into the device double `out`, using only the
+    library's built-in scratch (no device allocation)."""
+    cfg = scsc_config(int(K), int(s), float(lam), 1, 1, 0, SCSC_FP32, 0.0)
+    _check(lib().scsc_objective_noalloc(ctypes.byref(cfg), n_images, H, W, _ptr(x), _ptr(z),
+                                        _ptr(d), _ptr(out), c_void_p(_stream_handle(stream))),
+           None, "scsc_objective_noalloc")
 
 
 def scsc_sync(ctx: Context) -> None:
