@@ -38,6 +38,9 @@ WORKLOADS = {
                desc="64 x 256x256 blob images, K=100 11x11, p=1/4, lambda=1, 100 PG its/step"),
     "c1": dict(n=1, H=100, W=100, K=16, p=(1, 2), n_iters=20,
                desc="1 x 100x100 blob image, K=16 11x11, p=1/2, lambda=1, 20 PG its/step"),
+    "prof": dict(n=8, H=256, W=256, K=100, p=(1, 4), n_iters=4,
+                 desc="8 x 256x256 blob images, K=100 11x11, p=1/4, lambda=1, 4 PG its/step "
+                      "(small case for profiler captures)"),
     "c5": dict(n=512, H=None, W=None, K=100, p=(1, 4), n_iters=20,
                desc="512 blob images, H,W uniform in {64..512}, K=100 11x11, p=1/4, 20 PG its/step"),
 }

@@ -21,77 +21,17 @@
 
 #include "scsc_internal.cuh"
 #include "scsc_tc.cuh"
+#include "tc_items.cuh"
 #include "tc_ptx.cuh"
 
 namespace scsc {
 namespace {
 
-constexpr int kStrip = 128;
+using namespace tcitems;
 constexpr int kThreads = 128;
 constexpr uint64_t kWaitNs = 1000000000ull;  // bounded waits: 1 s
 constexpr int kPad = 10;                     // col2im padding (>= 2c)
 constexpr int kPuRow = kStrip + 2 * kPad;    // 148
-
-struct ItemMap {
-  int n;
-  const int *item0;  // [n + 1]
-  const int *H;
-  const int *W;
-  const int64_t *off;
-  int total;
-};
-
-struct Item {
-  int n, js, a, H, W, JS;
-  int64_t base;
-  int q_row0;  // item index of row 0 of this strip
-};
-
-__device__ __forceinline__ Item item_of(const ItemMap &m, int q) {
-  Item it;
-  it.n = upper_index(m.item0, m.n, q);
-  it.H = m.H[it.n];
-  it.W = m.W[it.n];
-  it.JS = (it.W + kStrip - 1) / kStrip;
-  int local = q - m.item0[it.n];
-  it.js = local / it.H;
-  it.a = local - it.js * it.H;
-  it.base = m.off[it.n];
-  it.q_row0 = q - it.a;
-  return it;
-}
-
-// 16-bit sampled mask of chunk c (filters 16c..16c+15) of pixel (a, col).
-__device__ __forceinline__ uint32_t chunk_mask(const uint32_t *bits, int KW, const Item &it, int a,
-                                               int col, int c) {
-  if (col >= it.W || a < 0 || a >= it.H) return 0u;
-  int64_t pix = it.base + (int64_t)a * it.W + col;
-  return (bits[pix * KW + (c >> 1)] >> ((c & 1) * 16)) & 0xFFFFu;
-}
-
-// Exclusive scan of one int per thread over a 128-thread block.
-__device__ __forceinline__ int scan128(int v, int *sh, int &total) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) sh[w] = x;
-  __syncthreads();
-  int pre = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) pre += (i < w) ? sh[i] : 0;
-  total = sh[0] + sh[1] + sh[2] + sh[3];
-  __syncthreads();
-  return pre + x - v;
-}
-
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
-  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t *>(&h);
-}
 
 // ------------------------------------------------------------------ filter images
 // B operand of the adjoint: per tap row u a [Kp filters x 16 taps] K-major
@@ -133,10 +73,14 @@ __global__ void __launch_bounds__(kThreads) seg_count_kernel(ItemMap im, int KW,
   const int q = blockIdx.x;
   const Item it = item_of(im, q);
   const int col = it.js * kStrip + threadIdx.x;
+  int item_total = 0;
   for (int c = 0; c < NC; ++c) {
     int cnt = __popc(chunk_mask(bits, KW, it, it.a, col, c));
     int total;
     scan128(cnt, sh, total);
+    item_total += total;
+    // the last chunk carries the padding that keeps every item 16-byte aligned
+    if (c == NC - 1) total += (4 - (item_total & 3)) & 3;
     if (threadIdx.x == 0) counts[(int64_t)q * NC + c] = (uint32_t)total;
   }
 }
@@ -243,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
   constexpr int C = L::C, N = L::N;
   const int NC = Kp / 16;
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *As = smem;
   uint8_t *Bs = As + L::a_bytes(Kp);
   float *stage = reinterpret_cast<float *>(Bs + L::b_bytes(Kp));
@@ -453,7 +397,7 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
   const int NC = Kp / 16;
   const int tcols = tmem_cols_for(Kp);
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *Bs = smem;
   uint8_t *ring = Bs + L::b_bytes(Kp);
   float *rstage = reinterpret_cast<float *>(ring + (size_t)S * L::kSRow);
@@ -588,7 +532,7 @@ __global__ void __launch_bounds__(kThreads) selftest_gemm_kernel(int N, const fl
                                                                  const float *B, float *D,
                                                                  int *err) {
   extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *As = smem;                  // 128 x 64 bf16 = 16 KB
   uint8_t *Bs = smem + 128 * 64 * 2;   // N x 64 bf16
   __shared__ uint64_t mbar;
@@ -688,6 +632,14 @@ T *as(const TcWorkspace::Buf &b) {
 
 }  // namespace
 
+cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
+                        const uint64_t *seg_base, const float *packed, const uint4 *bsyn,
+                        float *xcore, float *spill, int *err, int grid, int max_smem,
+                        cudaStream_t st);
+cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
+                        const uint64_t *seg_base, float *packed, const uint4 *badj, const float *r,
+                        const StepParams *prm, int *err, int grid, cudaStream_t st);
+
 int *tc_error_word(TcWorkspace &ws) {
   if (ensure(ws.err, sizeof(int)) != cudaSuccess) return nullptr;
   return as<int>(ws.err);
@@ -748,7 +700,7 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   TRY(ensure(ws.seg_count, (size_t)nseg * 4));
   TRY(ensure(ws.seg_base, (size_t)(nseg + 1) * 8));
   TRY(ensure(ws.scan_blocks, (size_t)(nblk + 1) * 8));
-  TRY(ensure(ws.packed, (size_t)b.total_px * K * 4 + 16));
+  TRY(ensure(ws.packed, ((size_t)b.total_px * K + 4 * (size_t)Q + 16) * 4));
   TRY(ensure(ws.xcore, (size_t)b.total_px * 4));
   TRY(ensure(ws.r, (size_t)b.total_px * 4));
   TRY(ensure(ws.spill, (size_t)Q * (2 * C > 0 ? 2 * C : 1) * 4));
@@ -776,7 +728,31 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   TRY(cudaGetLastError());
   if (ws.prof) ws.prof->end(pr, st);
 
-  TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
+  if (ws.max_smem == 0) {
+    int dev;
+    TRY(cudaGetDevice(&dev));
+    TRY(cudaDeviceGetAttribute(&ws.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  }
+  if (tc_pipe_supported(K, s, ws.max_smem)) {
+    const int grid = std::min(Q, ws.sm_count);
+    const int fin_grid = (int)std::min<int64_t>((b.total_px + 255) / 256, 152 * 16);
+    for (int it = 0; it < n_iters; ++it) {
+      int p1 = ws.prof ? ws.prof->begin(KID_SYNTH_TC, st) : -1;
+      TRY(launch_syn2(im, K, s, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.bsyn),
+                      as<float>(ws.xcore), as<float>(ws.spill), as<int>(ws.err), grid,
+                      ws.max_smem, st));
+      if (ws.prof) ws.prof->end(p1, st);
+      int p2 = ws.prof ? ws.prof->begin(KID_FINALIZE, st) : -1;
+      finalize_r_kernel<<<fin_grid, 256, 0, st>>>(b, im, C, as<float>(ws.xcore),
+                                                   as<float>(ws.spill), x, as<float>(ws.r));
+      TRY(cudaGetLastError());
+      if (ws.prof) ws.prof->end(p2, st);
+      int p3 = ws.prof ? ws.prof->begin(KID_ADJ_TC, st) : -1;
+      TRY(launch_adj2(im, K, s, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.badj),
+                      as<float>(ws.r), prm, as<int>(ws.err), grid, st));
+      if (ws.prof) ws.prof->end(p3, st);
+    }
+  } else TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
     const size_t smem_syn = SynthSmem<S>::total(Kp), smem_adj = AdjSmem<S>::total(Kp);
     auto ks = synth_tc_kernel<S>;

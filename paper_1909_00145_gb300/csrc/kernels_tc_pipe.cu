@@ -1,0 +1,842 @@
+// kernels_tc_pipe.cu -- warp-specialised, pipelined tcgen05 kernels of the
+// code update for K <= 128 (one persistent CTA per SM, 8 warps).
+//
+// Adjoint + prox (Eq. 3): warps 1-3 build the Toeplitz BF16 rows of the
+// residual into a ring of shared-memory slots (residual rows fetched with
+// cp.async two rows ahead); warp 0 issues, per item, one MMA per tap row into
+// one of two TMEM accumulators; warps 4-7 prefetch the next item's packed
+// codes and mask words with cp.async, apply the soft-threshold step to the
+// sampled coordinates from the accumulator and write the item back.
+//
+// Synthesis: warps 0-3 prefetch packed codes and masks with cp.async, expand
+// them into the BF16 A operand and (thread 0) issue the MMAs P = Z D^T into
+// one of two TMEM accumulators; warps 4-7 fold P into output rows (col2im)
+// through a small shared-memory transpose and write the strip's core columns
+// and its 2c spill columns.
+//
+// Every wait is bounded; on timeout the CTA raises an abort flag, all roles
+// leave their loops, the MMAs already issued are waited for (bounded) and the
+// tensor memory is released.
+#include "scsc_tc.cuh"
+#include "tc_items.cuh"
+#include "tc_ptx.cuh"
+
+namespace scsc {
+namespace {
+
+using namespace tcitems;
+
+constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr int kPad = 10;
+constexpr int kPuRow = kStrip + 2 * kPad;
+constexpr int kMaxNC = 8;  // Kp <= 128
+
+// Offset the dynamic shared-memory base to a 1024-byte boundary by pointer
+// arithmetic on the shared array itself, so that the compiler keeps treating
+// every derived pointer as a shared-memory address (LDS/STS, not generic).
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p) {
+  return p + ((1024u - (tc::smem_u32(p) & 1023u)) & 1023u);
+}
+
+// Output-row segments of a CTA's item range [q, q_end): maximal runs of items
+// in one strip.  o0..o1 are the segment's rows.
+struct SegIter {
+  int q, q_end;
+  Item it;
+  int o0, o1;
+  __device__ bool next(const ItemMap &im) {
+    if (q >= q_end) return false;
+    it = item_of(im, q);
+    int seg_end = min(q_end, it.q_row0 + it.H);
+    o0 = it.a;
+    o1 = o0 + (seg_end - q);
+    q = seg_end;
+    return true;
+  }
+};
+
+// Per-pixel chunk masks and exclusive offsets of the pixel's sampled values
+// inside the item's packed storage, from the staged mask words; one 128-thread
+// group (named barrier `bar`), thread e = pixel e, warp w of the group.
+__device__ __forceinline__ void chunk_offsets(const uint32_t *mw_s, int KW, int NC, int e, int w,
+                                              int lane, int *tot, int bar, uint32_t (&m)[kMaxNC],
+                                              int (&off)[kMaxNC]) {
+  int cnt[kMaxNC], incl[kMaxNC];
+#pragma unroll
+  for (int c = 0; c < kMaxNC; ++c) {
+    m[c] = 0u;
+    if (c < NC) m[c] = (mw_s[e * KW + (c >> 1)] >> ((c & 1) * 16)) & 0xFFFFu;
+    cnt[c] = __popc(m[c]);
+    int x = cnt[c];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    incl[c] = x;
+  }
+  if (lane == 31) {
+#pragma unroll
+    for (int c = 0; c < kMaxNC; ++c) tot[w * kMaxNC + c] = incl[c];
+  }
+  tc::named_sync(bar, 128);
+  int base = 0;
+#pragma unroll
+  for (int c = 0; c < kMaxNC; ++c) {
+    int pre = 0, ct = 0;
+#pragma unroll
+    for (int w2 = 0; w2 < 4; ++w2) {
+      int v = tot[w2 * kMaxNC + c];
+      pre += (w2 < w) ? v : 0;
+      ct += v;
+    }
+    off[c] = base + pre + incl[c] - cnt[c];
+    base += ct;
+  }
+}
+
+// Issue cp.async copies of one item's packed codes [beg, end) (16-byte pieces)
+// and of its pixels' mask words into shared memory, as one commit group of
+// this thread.  `it` describes the item's strip; `a` is its row.
+__device__ __forceinline__ void prefetch_item(const Item &it, int a, uint64_t beg, uint64_t end,
+                                              int KW, const float *packed, const uint32_t *bits,
+                                              float *dv, uint32_t *dm, int e) {
+  const int nv4 = (int)((end - beg) >> 2);
+  for (int k = e; k < nv4; k += 128) tc::cp_async16(dv + 4 * k, packed + beg + 4 * (uint64_t)k);
+  const int b0 = it.js * kStrip;
+  const int npx = min(kStrip, it.W - b0);
+  const uint32_t *src = bits + (it.base + (int64_t)a * it.W + b0) * KW;
+  for (int k = e; k < kStrip * KW; k += 128) {
+    const bool in = k / KW < npx;
+    tc::cp_async4(dm + k, in ? src + k : bits, in ? 4u : 0u);
+  }
+  tc::cp_async_commit();
+}
+
+// Item following `it` (next row of the strip, or the first row of the next
+// strip / image, found by search only at strip ends).
+__device__ __forceinline__ Item next_item(const ItemMap &im, const Item &it) {
+  if (it.a + 1 < it.H) {
+    Item n = it;
+    n.a += 1;
+    return n;
+  }
+  return item_of(im, it.q_row0 + it.H);
+}
+
+// ================================================================== adjoint + prox
+
+template <int S>
+struct Adj2 {
+  static constexpr int C = (S - 1) / 2;
+  static constexpr int RS = ((S + 3) + 1) & ~1;  // ring slots (even)
+  static constexpr int kSRow = 17 * 128;
+  static constexpr int kProd = 3;
+  __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)S * Kp * 32; }
+  __host__ __device__ static size_t vals_bytes(int Kp) { return (size_t)kStrip * Kp * 4; }
+  __host__ __device__ static size_t mask_bytes(int KW) { return (size_t)kStrip * KW * 4; }
+  __host__ __device__ static size_t total(int Kp, int KW) {
+    return 1024 + b_bytes(Kp) + (size_t)RS * kSRow + 2 * (vals_bytes(Kp) + mask_bytes(KW)) +
+           (size_t)kProd * 2 * 144 * 4 + 4 * kMaxNC * 4;
+  }
+};
+
+// Rows of the residual that the ring holds, in the order the MMA consumes
+// them: per segment, rows o0 - c .. o1 - 1 + c; j counts them across segments.
+struct RowGen {
+  SegIter sg;
+  int64_t j_seg, j;
+  int t, nrows;
+  bool live;
+  int C;
+  __device__ void init(int q0, int q1, int c) {
+    sg.q = q0;
+    sg.q_end = q1;
+    j_seg = 0;
+    j = 0;
+    t = 0;
+    nrows = 0;
+    live = false;
+    C = c;
+  }
+  // Advance to the next row; false when exhausted.
+  __device__ bool next(const ItemMap &im) {
+    while (!live || t >= nrows) {
+      if (live) j_seg += nrows;
+      if (!sg.next(im)) return false;
+      live = true;
+      t = 0;
+      nrows = sg.o1 - sg.o0 + 2 * C;
+    }
+    j = j_seg + t;
+    ++t;
+    return true;
+  }
+  __device__ int ar() const { return sg.o0 - C + (t - 1); }
+};
+
+template <int S>
+__global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp, int KW,
+                                                      const uint32_t *__restrict__ bits,
+                                                      const uint64_t *__restrict__ seg_base,
+                                                      float *__restrict__ packed,
+                                                      const uint4 *__restrict__ badj,
+                                                      const float *__restrict__ r,
+                                                      const StepParams *__restrict__ prm,
+                                                      int *err) {
+  using L = Adj2<S>;
+  constexpr int C = L::C, RS = L::RS;
+  const int NC = Kp / 16;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = align1024(smem_raw);
+  uint8_t *Bs = smem;
+  uint8_t *ring = Bs + L::b_bytes(Kp);
+  uint8_t *p = ring + (size_t)RS * L::kSRow;
+  float *const vals0 = reinterpret_cast<float *>(p);
+  p += L::vals_bytes(Kp);
+  float *const vals1 = reinterpret_cast<float *>(p);
+  p += L::vals_bytes(Kp);
+  uint32_t *const msk0 = reinterpret_cast<uint32_t *>(p);
+  p += L::mask_bytes(KW);
+  uint32_t *const msk1 = reinterpret_cast<uint32_t *>(p);
+  p += L::mask_bytes(KW);
+  auto vals = [&](int k) { return (k & 1) ? vals1 : vals0; };
+  auto msk = [&](int k) { return (k & 1) ? msk1 : msk0; };
+  float *rst = reinterpret_cast<float *>(p);
+  p += (size_t)L::kProd * 2 * 144 * 4;
+  int *tot = reinterpret_cast<int *>(p);
+
+  __shared__ uint64_t ring_full[RS], ring_empty[RS], tfull[2], tempty[2], done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 256);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < RS; ++i) {
+      tc::mbar_init(&ring_full[i], 1);
+      tc::mbar_init(&ring_empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&tfull[i], 1);
+      tc::mbar_init(&tempty[i], 4);
+    }
+    tc::mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  {
+    const int n16 = (int)(L::b_bytes(Kp) / 16);
+    uint4 *dst = reinterpret_cast<uint4 *>(Bs);
+    for (int i = tid; i < n16; i += blockDim.x) dst[i] = badj[i];
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base;
+  const int Q = im.total;
+  const int q_begin = (int)((int64_t)Q * blockIdx.x / gridDim.x);
+  const int q_end = (int)((int64_t)Q * (blockIdx.x + 1) / gridDim.x);
+  volatile int *abort_v = &abort_flag;
+
+  if (warp == 0) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(128, Kp);
+      const uint32_t ring_base = tc::smem_u32(ring), b_base = tc::smem_u32(Bs);
+      SegIter sg{q_begin, q_end};
+      int64_t j_seg = 0;
+      int i = 0;
+      bool ok = true;
+      while (ok && sg.next(im)) {
+        const int nrows = sg.o1 - sg.o0 + 2 * C;
+        for (int a = sg.o0; a < sg.o1; ++a, ++i) {
+          const int b = i & 1;
+          const uint32_t use = (uint32_t)(i >> 1);
+          ok = tc::mbar_wait_abortable(&tempty[b], (use & 1u) ^ 1u, abort_v, kWaitNs);
+          const int64_t jr = j_seg + (a - sg.o0);
+          for (int u = 0; u < S && ok; ++u) {
+            const int64_t j = jr + u;
+            ok = tc::mbar_wait_abortable(&ring_full[j % RS], (uint32_t)((j / RS) & 1), abort_v,
+                                         kWaitNs);
+          }
+          if (!ok) break;
+          tc::fence_after_sync();
+#pragma unroll 1
+          for (int u = 0; u < S; ++u) {
+            const uint32_t slot = (uint32_t)((jr + u) % RS);
+            uint64_t ad = tc::smem_desc(ring_base + slot * L::kSRow, 128, 128);
+            uint64_t bd = tc::smem_desc(b_base + u * Kp * 32, Kp * 16, 128);
+            tc::mma_bf16(taddr + b * 128, ad, bd, idesc, u > 0 ? 1u : 0u);
+          }
+          tc::mma_commit(&tfull[b]);
+          tc::mma_commit(&ring_empty[jr % RS]);
+          if (a == sg.o1 - 1)
+            for (int e2 = 1; e2 <= 2 * C; ++e2) tc::mma_commit(&ring_empty[(jr + e2) % RS]);
+        }
+        j_seg += nrows;
+      }
+      tc::mma_commit(&done_bar);
+      tc::mbar_wait_bounded(&done_bar, 0, kWaitNs);
+    }
+  } else if (warp <= L::kProd) {
+    // ------------------------------------------------ residual row producers
+    const int pw = warp - 1;
+    float *const stg0 = rst + pw * 2 * 144, *const stg1 = stg0 + 144;
+    RowGen g;
+    g.init(q_begin, q_end, C);
+    // rows of this warp: sequence indices j = pw (mod kProd)
+    auto next_mine = [&](RowGen &gg) -> bool {
+      while (gg.next(im))
+        if ((int)(gg.j % L::kProd) == pw) return true;
+      return false;
+    };
+    auto issue = [&](const RowGen &gg, float *dst) {
+      const Item &it = gg.sg.it;
+      const int ar = gg.ar(), b0 = it.js * kStrip;
+      for (int k = lane; k < 144; k += 32) {
+        const int col = b0 - C + k;
+        const bool in = ar >= 0 && ar < it.H && col >= 0 && col < it.W;
+        tc::cp_async4(dst + k, in ? r + it.base + (int64_t)ar * it.W + col : r, in ? 4u : 0u);
+      }
+      tc::cp_async_commit();
+    };
+    RowGen cur = g;
+    bool have = next_mine(cur);
+    if (have) issue(cur, stg0);
+    int sbuf = 0;
+    bool ok = true;
+    while (have && ok) {
+      RowGen nxt = cur;
+      bool have_next = next_mine(nxt);
+      if (have_next) issue(nxt, sbuf ? stg0 : stg1);
+      else tc::cp_async_commit();
+      const int64_t j = cur.j;
+      const int slot = (int)(j % RS);
+      bool w = true;
+      if (lane == 0)
+        w = tc::mbar_wait_abortable(&ring_empty[slot], (uint32_t)(((j / RS) & 1) ^ 1), abort_v,
+                                    kWaitNs);
+      w = __shfl_sync(0xffffffffu, w, 0);
+      if (!w) {
+        ok = false;
+        break;
+      }
+      tc::cp_async_wait<1>();
+      __syncwarp();
+      const float *src0 = sbuf ? stg1 : stg0;
+      uint8_t *dst = ring + (size_t)slot * L::kSRow;
+      for (int t2 = lane; t2 < 17 * 8; t2 += 32) {
+        const int gq = t2 >> 3, ii = t2 & 7;
+        const float *src = src0 + 8 * gq + ii;
+        uint4 v = make_uint4(pack_bf16x2(src[0], src[1]), pack_bf16x2(src[2], src[3]),
+                             pack_bf16x2(src[4], src[5]), pack_bf16x2(src[6], src[7]));
+        *reinterpret_cast<uint4 *>(dst + gq * 128 + ii * 16) = v;
+      }
+      tc::fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&ring_full[slot]);
+      cur = nxt;
+      have = have_next;
+      sbuf ^= 1;
+    }
+    tc::cp_async_wait<0>();
+  } else {
+    // ------------------------------------------------ epilogue: prox on packed codes
+    const int e = tid - 128, ew = e >> 5;
+    const float alpha = prm->alpha, thr = prm->thresh;
+    const int n_items = q_end - q_begin;
+    const int Qv = Q;
+    (void)Qv;
+    const uint32_t lane_base = taddr + ((uint32_t)(32 * ew) << 16);
+    // item bookkeeping one step ahead: cur = item i, nxt = item i + 1;
+    // b0v..b2v = seg_base of items i, i + 1, i + 2 (b3v loaded a step early)
+    Item cur = item_of(im, q_begin), nxt = cur;
+    uint64_t b0v = 0, b1v = 0, b2v = 0;
+    if (n_items > 0) {
+      b0v = seg_base[(int64_t)q_begin * NC];
+      b1v = seg_base[(int64_t)(q_begin + 1) * NC];
+      prefetch_item(cur, cur.a, b0v, b1v, KW, packed, bits, vals(0), msk(0), e);
+      if (n_items > 1) nxt = next_item(im, cur);
+      b2v = seg_base[(int64_t)min(q_begin + 2, Q) * NC];
+    }
+    for (int i = 0; i < n_items; ++i) {
+      const int q = q_begin + i;
+      const uint64_t b3v = seg_base[(int64_t)min(q + 3, Q) * NC];
+      if (i + 1 < n_items)
+        prefetch_item(nxt, nxt.a, b1v, b2v, KW, packed, bits, vals((i + 1) & 1),
+                      msk((i + 1) & 1), e);
+      else
+        tc::cp_async_commit();
+      tc::cp_async_wait<1>();
+      tc::named_sync(2, 128);
+      uint32_t m[kMaxNC];
+      int off[kMaxNC];
+      chunk_offsets(msk(i & 1), KW, NC, e, ew, lane, tot, 2, m, off);
+      const int b = i & 1;
+      bool okw = true;
+      if (e == 0)
+        okw = tc::mbar_wait_abortable(&tfull[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
+      if (tc::named_sync_or(2, 128, !okw)) break;
+      tc::fence_after_sync();
+      float *dv = vals(i & 1);
+      uint32_t g[32];  // accumulator columns of two chunks (32 filters)
+#pragma unroll
+      for (int c = 0; c < kMaxNC; ++c) {
+        if (c >= NC) break;
+        if ((c & 1) == 0) {
+          __syncwarp();
+          tc::tmem_ld32_nowait(lane_base + b * 128 + 16 * c, g);
+          tc::tmem_ld_wait();
+        }
+        // slot of filter e2 = chunk offset + number of sampled filters below e2:
+        // all loads are independent, then all stores
+        // Loads are unconditional (an unsampled slot's index still lies inside
+        // the staged item) and stores predicated, so the loop has no branches.
+        const uint32_t dbase = tc::smem_u32(dv) + 4u * (uint32_t)off[c];
+        float zv[16];
+#pragma unroll
+        for (int e2 = 0; e2 < 16; ++e2)
+          zv[e2] = tc::ld_shared(dbase + 4u * __popc(m[c] & ((1u << e2) - 1u)));
+#pragma unroll
+        for (int e2 = 0; e2 < 16; ++e2) {
+          const float gv = __uint_as_float(g[(c & 1) * 16 + e2]);
+          tc::st_shared_if(dbase + 4u * __popc(m[c] & ((1u << e2) - 1u)),
+                           soft_threshold(zv[e2] - alpha * gv, thr), (m[c] >> e2) & 1u);
+        }
+      }
+      tc::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&tempty[b]);
+      tc::named_sync(2, 128);
+      const int nv4 = (int)((b1v - b0v) >> 2);
+      for (int k = e; k < nv4; k += 128)
+        *reinterpret_cast<float4 *>(packed + b0v + 4 * (uint64_t)k) =
+            *reinterpret_cast<const float4 *>(dv + 4 * k);
+      tc::named_sync(2, 128);  // the buffer is refilled by the prefetch two items on
+      b0v = b1v;
+      b1v = b2v;
+      b2v = b3v;
+      if (i + 2 < n_items) nxt = next_item(im, nxt);
+    }
+    tc::cp_async_wait<0>();
+  }
+
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, 256);
+  }
+  if (tid == 0 && abort_flag) atomicExch(err, 1);
+}
+
+// ================================================================== synthesis
+
+template <int S>
+struct Syn2 {
+  static constexpr int C = (S - 1) / 2;
+  static constexpr int N = 16 * S;
+  __host__ __device__ static size_t a_bytes(int Kp) { return (size_t)kStrip * Kp * 2; }
+  __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)N * Kp * 2; }
+  __host__ __device__ static size_t vals_bytes(int Kp) { return (size_t)kStrip * Kp * 4; }
+  __host__ __device__ static size_t mask_bytes(int KW) { return (size_t)kStrip * KW * 4; }
+  __host__ __device__ static size_t total(int Kp, int KW, int nst) {
+    return 1024 + a_bytes(Kp) + b_bytes(Kp) + (size_t)nst * (vals_bytes(Kp) + mask_bytes(KW)) +
+           (size_t)2 * 4 * 2 * S * S * 4 + 4 * kMaxNC * 4;
+  }
+};
+
+// Code rows a synthesis CTA visits: per segment, rows max(0, o0-c) ..
+// min(H, o1+c) - 1 of the segment's strip.
+struct CodeRowGen {
+  SegIter sg;
+  int a, a_end;
+  bool live;
+  int C;
+  __device__ void init(int q0, int q1, int c) {
+    sg.q = q0;
+    sg.q_end = q1;
+    live = false;
+    C = c;
+    a = a_end = 0;
+  }
+  __device__ bool next(const ItemMap &im) {
+    if (live) ++a;
+    while (!live || a >= a_end) {
+      if (!sg.next(im)) return false;
+      live = true;
+      a = max(0, sg.o0 - C);
+      a_end = min(sg.it.H, sg.o1 + C);
+    }
+    return true;
+  }
+  __device__ int q() const { return sg.it.q_row0 + a; }
+};
+
+template <int S>
+__global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp, int KW, int nst,
+                                                      const uint32_t *__restrict__ bits,
+                                                      const uint64_t *__restrict__ seg_base,
+                                                      const float *__restrict__ packed,
+                                                      const uint4 *__restrict__ bsyn,
+                                                      float *__restrict__ xcore,
+                                                      float *__restrict__ spill, int *err) {
+  using L = Syn2<S>;
+  constexpr int C = L::C, N = L::N;
+  const int NC = Kp / 16;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = align1024(smem_raw);
+  uint8_t *As = smem;
+  uint8_t *Bs = As + L::a_bytes(Kp);
+  uint8_t *p = Bs + L::b_bytes(Kp);
+  float *const vals0 = reinterpret_cast<float *>(p);
+  p += L::vals_bytes(Kp);
+  float *vals1 = vals0;
+  if (nst == 2) {
+    vals1 = reinterpret_cast<float *>(p);
+    p += L::vals_bytes(Kp);
+  }
+  uint32_t *const msk0 = reinterpret_cast<uint32_t *>(p);
+  p += L::mask_bytes(KW);
+  uint32_t *msk1 = msk0;
+  if (nst == 2) {
+    msk1 = reinterpret_cast<uint32_t *>(p);
+    p += L::mask_bytes(KW);
+  }
+  auto vals = [&](int k) { return (k & 1) ? vals1 : vals0; };
+  auto msk = [&](int k) { return (k & 1) ? msk1 : msk0; };
+  float *Pu = reinterpret_cast<float *>(p);  // edge exchange of the col2im, [2][4][2c][S]
+  p += (size_t)2 * 4 * 2 * S * S * 4;
+  int *tot = reinterpret_cast<int *>(p);
+
+  __shared__ uint64_t tfull[2], tempty[2], a_free, done_bar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 512);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&tfull[i], 1);
+      tc::mbar_init(&tempty[i], 4);
+    }
+    tc::mbar_init(&a_free, 1);
+    tc::mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    tc::fence_mbar_init();
+  }
+  {
+    const int n16 = (int)(L::b_bytes(Kp) / 16);
+    uint4 *dst = reinterpret_cast<uint4 *>(Bs);
+    for (int i = tid; i < n16; i += blockDim.x) dst[i] = bsyn[i];
+    for (int i = tid; i < 2 * 4 * 2 * S * S; i += blockDim.x) Pu[i] = 0.0f;
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base;
+  const int Q = im.total;
+  const int q_begin = (int)((int64_t)Q * blockIdx.x / gridDim.x);
+  const int q_end = (int)((int64_t)Q * (blockIdx.x + 1) / gridDim.x);
+  volatile int *abort_v = &abort_flag;
+
+  if (warp < 4) {
+    // ------------------------------------------------ producers + MMA issue
+    const int e = tid, ew = warp;
+    const uint32_t idesc = tc::idesc_bf16_f32(128, N);
+    const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
+    const uint32_t b_lbo = 2 * S * 128;
+    // code rows in sequence: g (current), nx (next), nn (after next); the
+    // seg_base values of each row are loaded one iteration before they are used
+    auto base_of = [&](int qq) { return seg_base[(int64_t)qq * NC]; };
+    CodeRowGen g;
+    g.init(q_begin, q_end, C);
+    bool have = g.next(im);
+    CodeRowGen nx = g;
+    bool have_nx = have && nx.next(im);
+    uint64_t gb0 = 0, gb1 = 0, nb0 = 0, nb1 = 0;
+    if (have) {
+      gb0 = base_of(g.q());
+      gb1 = base_of(g.q() + 1);
+    }
+    if (have_nx) {
+      nb0 = base_of(nx.q());
+      nb1 = base_of(nx.q() + 1);
+    }
+    if (have && nst == 2)
+      prefetch_item(g.sg.it, g.a, gb0, gb1, KW, packed, bits, vals(0), msk(0), e);
+    int i = 0;
+    while (have) {
+      CodeRowGen nn = nx;
+      const bool have_nn = have_nx && nn.next(im);
+      uint64_t mb0 = 0, mb1 = 0;
+      if (have_nn) {
+        mb0 = base_of(nn.q());
+        mb1 = base_of(nn.q() + 1);
+      }
+      const int sb = nst == 2 ? (i & 1) : 0;
+      if (nst == 2) {
+        if (have_nx)
+          prefetch_item(nx.sg.it, nx.a, nb0, nb1, KW, packed, bits, vals((i + 1) & 1),
+                        msk((i + 1) & 1), e);
+        else
+          tc::cp_async_commit();
+        tc::cp_async_wait<1>();
+      } else {
+        prefetch_item(g.sg.it, g.a, gb0, gb1, KW, packed, bits, vals(0), msk(0), e);
+        tc::cp_async_wait<0>();
+      }
+      tc::named_sync(1, 128);
+      uint32_t m[kMaxNC];
+      int off[kMaxNC];
+      chunk_offsets(msk(sb), KW, NC, e, ew, lane, tot, 1, m, off);
+      bool okw = true;
+      if (e == 0 && i > 0)
+        okw = tc::mbar_wait_abortable(&a_free, (uint32_t)((i - 1) & 1), abort_v, kWaitNs);
+      if (tc::named_sync_or(1, 128, !okw)) break;
+      const float *dv = vals(sb);
+#pragma unroll
+      for (int c = 0; c < kMaxNC; ++c) {
+        if (c >= NC) break;
+        float v[16];
+        const uint32_t dbase = tc::smem_u32(dv) + 4u * (uint32_t)off[c];
+#pragma unroll
+        for (int e2 = 0; e2 < 16; ++e2) {
+          const float t = tc::ld_shared(dbase + 4u * __popc(m[c] & ((1u << e2) - 1u)));
+          v[e2] = ((m[c] >> e2) & 1u) ? t : 0.0f;
+        }
+        uint4 lo = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                              pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+        uint4 hi = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
+                              pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+        uint8_t *dst = As + (size_t)(2 * c) * 2048 + (e >> 3) * 128 + (e & 7) * 16;
+        *reinterpret_cast<uint4 *>(dst) = lo;
+        *reinterpret_cast<uint4 *>(dst + 2048) = hi;
+      }
+      tc::fence_proxy_async();
+      tc::named_sync(1, 128);
+      if (e == 0) {
+        const int b = i & 1;
+        bool okm = tc::mbar_wait_abortable(&tempty[b], (uint32_t)(((i >> 1) & 1) ^ 1), abort_v,
+                                           kWaitNs);
+        if (okm) {
+          tc::fence_after_sync();
+#pragma unroll 1
+          for (int kk = 0; kk < NC; ++kk) {
+            uint64_t ad = tc::smem_desc(a_base + kk * 2 * 2048, 2048, 128);
+            uint64_t bd = tc::smem_desc(b_base + kk * 2 * b_lbo, b_lbo, 128);
+            tc::mma_bf16(taddr + b * 256, ad, bd, idesc, kk > 0 ? 1u : 0u);
+          }
+          tc::mma_commit(&tfull[b]);
+          tc::mma_commit(&a_free);
+        }
+      }
+      g = nx;
+      have = have_nx;
+      gb0 = nb0;
+      gb1 = nb1;
+      nx = nn;
+      have_nx = have_nn;
+      nb0 = mb0;
+      nb1 = mb1;
+      ++i;
+    }
+    tc::cp_async_wait<0>();
+    if (tid == 0) {
+      tc::mma_commit(&done_bar);
+      tc::mbar_wait_bounded(&done_bar, 0, kWaitNs);
+    }
+  } else {
+    // ------------------------------------------------ epilogue: col2im
+    // Output column L of this warp gets sum_v P[L + c - v][(u, v)] by warp
+    // shuffles; contributions that cross a warp boundary are summed by the
+    // edge lanes (c lanes at each side) and exchanged once per code row; the
+    // strip's outer edges accumulate the spill columns.
+    const int e = tid - 128, ew = e >> 5;
+    const uint32_t lane_base = taddr + ((uint32_t)(32 * ew) << 16);
+    const bool left_edge = lane < C, right_edge = lane >= 32 - C;
+    const bool spill_lane = (ew == 0 && left_edge) || (ew == 3 && right_edge);
+    const int spill_slot = ew == 0 ? lane : lane - 32 + 2 * C;
+    SegIter sg{q_begin, q_end};
+    int i = 0;
+    bool ok = true;
+    while (ok && sg.next(im)) {
+      const int a_start = max(0, sg.o0 - C), a_end = min(sg.it.H, sg.o1 + C);
+      const int b0 = sg.it.js * kStrip;
+      const Item &it = sg.it;
+      float acc[S], acch[S];
+#pragma unroll
+      for (int u = 0; u < S; ++u) acc[u] = acch[u] = 0.0f;
+      for (int a = a_start; a < a_end; ++a, ++i) {
+        const int b = i & 1;
+        bool okw = true;
+        if (e == 0)
+          okw = tc::mbar_wait_abortable(&tfull[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
+        if (tc::named_sync_or(2, 128, !okw)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after_sync();
+        // tap rows in batches of kB TMEM loads (one wait per batch)
+        constexpr int kB = 4;
+        uint32_t pr[kB][16];
+        float hacc[S];
+#pragma unroll
+        for (int u = 0; u < S; ++u) {
+          if (u % kB == 0) {
+            __syncwarp();
+#pragma unroll
+            for (int w2 = 0; w2 < kB; ++w2)
+              if (u + w2 < S) tc::tmem_ld16_nowait(lane_base + b * 256 + 16 * (u + w2), pr[w2]);
+            tc::tmem_ld_wait();
+          }
+          float own0 = 0.0f, own1 = 0.0f, hal = 0.0f;
+#pragma unroll
+          for (int v = 0; v < S; ++v) {
+            const float pvv = __uint_as_float(pr[u % kB][v]);
+            const int so = lane + C - v;
+            const float t = __shfl_sync(0xffffffffu, pvv, so & 31);
+            const float tv = (so >= 0 && so < 32) ? t : 0.0f;
+            if (v & 1) own1 += tv;
+            else own0 += tv;
+            if (C > 0) {
+              const int sh = left_edge ? lane - v : lane + 2 * C - v;
+              const float th = __shfl_sync(0xffffffffu, pvv, sh & 31);
+              hal += (sh >= 0 && sh < 32) ? th : 0.0f;
+            }
+          }
+          acc[u] += own0 + own1;
+          hacc[u] = hal;
+        }
+        tc::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&tempty[b]);
+        if (C > 0) {
+          // edge partial sums: slot j < c = left halo column j - c (lane j),
+          // slot c + j = right halo column 32 + j (lane 32 - c + j)
+          float *xb = Pu + (i & 1) * (4 * 2 * C * S);
+          if (left_edge || right_edge) {
+            const int slot = left_edge ? lane : C + lane - (32 - C);
+#pragma unroll
+            for (int u = 0; u < S; ++u) xb[(ew * 2 * C + slot) * S + u] = hacc[u];
+          }
+          tc::named_sync(2, 128);
+          if (left_edge && ew > 0) {
+#pragma unroll
+            for (int u = 0; u < S; ++u) acc[u] += xb[((ew - 1) * 2 * C + C + lane) * S + u];
+          }
+          if (right_edge && ew < 3) {
+#pragma unroll
+            for (int u = 0; u < S; ++u) acc[u] += xb[((ew + 1) * 2 * C + lane - (32 - C)) * S + u];
+          }
+          if (spill_lane) {
+#pragma unroll
+            for (int u = 0; u < S; ++u) acch[u] += hacc[u];
+          }
+        }
+        const int o = a - C;
+        if (o >= sg.o0 && o < sg.o1) {
+          if (b0 + e < it.W) xcore[it.base + (int64_t)o * it.W + b0 + e] = acc[0];
+          if (spill_lane) spill[(int64_t)(it.q_row0 + o) * (2 * C) + spill_slot] = acch[0];
+        }
+#pragma unroll
+        for (int u = 0; u < S - 1; ++u) {
+          acc[u] = acc[u + 1];
+          acch[u] = acch[u + 1];
+        }
+        acc[S - 1] = acch[S - 1] = 0.0f;
+      }
+      if (!ok) break;
+#pragma unroll
+      for (int j = 0; j < S - 1; ++j) {
+        const int o = a_end - C + j;
+        if (o >= sg.o0 && o < sg.o1 && o < it.H) {
+          if (b0 + e < it.W) xcore[it.base + (int64_t)o * it.W + b0 + e] = acc[j];
+          if (spill_lane) spill[(int64_t)(it.q_row0 + o) * (2 * C) + spill_slot] = acch[j];
+        }
+      }
+    }
+  }
+
+  __syncthreads();
+  if (warp == 0) {
+    __syncwarp();
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, 512);
+  }
+  if (tid == 0 && abort_flag) atomicExch(err, 1);
+}
+
+template <typename F>
+cudaError_t dispatch_s(int s, F &&f) {
+  switch (s) {
+    case 1: return f(std::integral_constant<int, 1>());
+    case 3: return f(std::integral_constant<int, 3>());
+    case 5: return f(std::integral_constant<int, 5>());
+    case 7: return f(std::integral_constant<int, 7>());
+    case 9: return f(std::integral_constant<int, 9>());
+    case 11: return f(std::integral_constant<int, 11>());
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+bool tc_pipe_supported(int K, int s, int max_smem) {
+  const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
+  if (Kp > 128) return false;
+  size_t need = 0;
+  dispatch_s(s, [&](auto SC) -> cudaError_t {
+    constexpr int S = decltype(SC)::value;
+    need = Adj2<S>::total(Kp, KW);
+    size_t syn = Syn2<S>::total(Kp, KW, 1);
+    if (syn > need) need = syn;
+    return cudaSuccess;
+  });
+  return need > 0 && need <= (size_t)max_smem;
+}
+
+cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
+                        const uint64_t *seg_base, const float *packed, const uint4 *bsyn,
+                        float *xcore, float *spill, int *err, int grid, int max_smem,
+                        cudaStream_t st) {
+  const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
+  return dispatch_s(s, [&](auto SC) -> cudaError_t {
+    constexpr int S = decltype(SC)::value;
+    int nst = Syn2<S>::total(Kp, KW, 2) <= (size_t)max_smem ? 2 : 1;
+    const size_t smem = Syn2<S>::total(Kp, KW, nst);
+    cudaError_t e = cudaFuncSetAttribute(syn2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    syn2_kernel<S><<<grid, 256, smem, st>>>(im, K, Kp, KW, nst, bits, seg_base, packed, bsyn,
+                                            xcore, spill, err);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
+                        const uint64_t *seg_base, float *packed, const uint4 *badj, const float *r,
+                        const StepParams *prm, int *err, int grid, cudaStream_t st) {
+  const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
+  return dispatch_s(s, [&](auto SC) -> cudaError_t {
+    constexpr int S = decltype(SC)::value;
+    const size_t smem = Adj2<S>::total(Kp, KW);
+    cudaError_t e = cudaFuncSetAttribute(adj2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    adj2_kernel<S><<<grid, 256, smem, st>>>(im, K, Kp, KW, bits, seg_base, packed, badj, r, prm,
+                                            err);
+    return cudaGetLastError();
+  });
+}
+
+}  // namespace scsc

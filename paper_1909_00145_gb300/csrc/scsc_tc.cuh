@@ -20,6 +20,7 @@ struct TcWorkspace {
   std::vector<int> host_H, host_W;
   int n_items = 0;
   int sm_count = 0;
+  int max_smem = 0;
   Profiler *prof = nullptr;  // the owning context's profiler
   std::string last_error;
 };
@@ -42,6 +43,10 @@ const char *tc_last_error(const TcWorkspace &ws);
 // operands rounded from the float inputs, FP32 accumulation); device buffers.
 cudaError_t tc_selftest_gemm(int N, const float *A, const float *B, float *D, int *err,
                              cudaStream_t st);
+
+// Pipelined tensor kernels (kernels_tc_pipe.cu): K <= 128 and shared memory
+// within `max_smem` bytes per block.
+bool tc_pipe_supported(int K, int s, int max_smem);
 
 // Helpers implemented in kernels_online.cu.
 cudaError_t launch_surrogate_update(const BatchDev &b, int K, int s, const float *z, const float *x,

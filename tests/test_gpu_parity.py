@@ -211,3 +211,19 @@ def test_dict_step_online_fp32_and_state_roundtrip():
     _, _, z = make_case(H, W, K, s, seed=23, code_density=0.2)
     ctx2.dict_step(b, dev(x), dev(z), d_saved, scsc.SCSC_DICT_ONLINE, 3)
     assert torch.equal(d_saved, dt)
+
+
+def test_code_step_bf16_large_k_fallback_kernels():
+    """128 < K <= 256 runs the single-stage tensor kernels."""
+    zg, zo, fg, fo, _ = run_code_step("bf16", 150, 5, [20, 9], [70, 140], (1, 4), 6, seed=4, lam=0.6)
+    assert fg == pytest.approx(fo, rel=1e-3)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_code_step_many_items_per_cta(prec):
+    """A batch with many more 128-pixel row items than SMs, so that each
+    persistent CTA crosses strip and image boundaries."""
+    H, W = [50] * 24, [260] * 24
+    zg, zo, fg, fo, _ = run_code_step(prec, 32, 7, H, W, (1, 4), 6, seed=6, lam=0.7)
+    assert fg == pytest.approx(fo, rel=1e-5 if prec == "fp32" else 1e-3)
+    assert rel_l2(zg, zo) < (1e-4 if prec == "fp32" else 5e-2)
