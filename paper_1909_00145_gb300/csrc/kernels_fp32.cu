@@ -5,6 +5,8 @@
 //
 // Spatial tiles are 32 x 32 pixels.  Codes are float32 [pixel][K]; images are
 // packed back to back (see scsc.h).
+#include <algorithm>
+
 #include "scsc_internal.cuh"
 
 namespace scsc {
@@ -72,8 +74,10 @@ __global__ void apply_mask_dense_kernel(int64_t total, int K, int KW, const uint
 // out(i,j) = sum_k sum_{u,v} d_k(u,v) z_k(i+c-u, j+c-v)  [- x(i,j)]
 // 128 threads; thread (tx, ty) owns column tx and rows 8 ty .. 8 ty + 7.
 
+// gridDim.y > 1 splits the filters into gridDim.y ranges of `kspan`; each
+// range writes its partial sum to out + blockIdx.y * total_px (no residual).
 template <int S, int KC>
-__global__ void __launch_bounds__(128) synth_fp32_kernel(BatchDev b, int K,
+__global__ void __launch_bounds__(128) synth_fp32_kernel(BatchDev b, int K, int kspan,
                                                          const float *__restrict__ d,
                                                          const float *__restrict__ z,
                                                          const uint32_t *__restrict__ bits,
@@ -91,7 +95,8 @@ __global__ void __launch_bounds__(128) synth_fp32_kernel(BatchDev b, int K,
 #pragma unroll
   for (int r = 0; r < R; ++r) acc[r] = 0.0f;
 
-  for (int k0 = 0; k0 < K; k0 += KC) {
+  const int kbeg = blockIdx.y * kspan, kend = min(K, kbeg + kspan);
+  for (int k0 = kbeg; k0 < kend; k0 += KC) {
     __syncthreads();
     for (int i = threadIdx.x; i < HS * HS; i += blockDim.x) {
       int hy = i / HS, hx = i - hy * HS;
@@ -102,7 +107,7 @@ __global__ void __launch_bounds__(128) synth_fp32_kernel(BatchDev b, int K,
       for (int kk = 0; kk < KC; ++kk) {
         int k = k0 + kk;
         float v = 0.0f;
-        if (in && k < K) {
+        if (in && k < kend) {
           v = z[pix * K + k];
           if (bits != nullptr && !bit_of(bits, pix, KW, k)) v = 0.0f;
         }
@@ -111,7 +116,7 @@ __global__ void __launch_bounds__(128) synth_fp32_kernel(BatchDev b, int K,
     }
     for (int i = threadIdx.x; i < KC * S * S; i += blockDim.x) {
       int kk = i / (S * S), m = i - kk * S * S;
-      ds[kk][m] = (k0 + kk < K) ? d[(int64_t)(k0 + kk) * S * S + m] : 0.0f;
+      ds[kk][m] = (k0 + kk < kend) ? d[(int64_t)(k0 + kk) * S * S + m] : 0.0f;
     }
     __syncthreads();
 #pragma unroll 1
@@ -135,8 +140,20 @@ __global__ void __launch_bounds__(128) synth_fp32_kernel(BatchDev b, int K,
     int i = tc.y0 + ty * R + r, j = tc.x0 + tx;
     if (i < tc.H && j < tc.W) {
       int64_t p = tc.base + (int64_t)i * tc.W + j;
-      out[p] = x != nullptr ? acc[r] - x[p] : acc[r];
+      if (gridDim.y > 1) out[blockIdx.y * b.total_px + p] = acc[r];
+      else out[p] = x != nullptr ? acc[r] - x[p] : acc[r];
     }
+  }
+}
+
+// out[p] = sum_s part[s][p] (- x[p]), fixed order over s.
+__global__ void sum_split_kernel(const float *__restrict__ part, int nsplit, int64_t n,
+                                 const float *__restrict__ x, float *__restrict__ out) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    float v = 0.0f;
+    for (int s2 = 0; s2 < nsplit; ++s2) v += part[s2 * n + p];
+    out[p] = x != nullptr ? v - x[p] : v;
   }
 }
 
@@ -175,7 +192,9 @@ __global__ void __launch_bounds__(128) adjoint_fp32_kernel(BatchDev b, int K,
     bool in = yy >= 0 && yy < tc.H && xx >= 0 && xx < tc.W;
     rs[hy][hx] = in ? r[tc.base + (int64_t)yy * tc.W + xx] : 0.0f;
   }
-  for (int kc0 = 0; kc0 < K; kc0 += KCH) {
+  const int kspan = (K + gridDim.y - 1) / gridDim.y;
+  const int kbeg = blockIdx.y * ((kspan + KCH - 1) / KCH) * KCH;
+  for (int kc0 = kbeg; kc0 < K && kc0 < kbeg + ((kspan + KCH - 1) / KCH) * KCH; kc0 += KCH) {
     __syncthreads();
     for (int i = threadIdx.x; i < KCH * S * S; i += blockDim.x) {
       int kk = i / (S * S), m = i - kk * S * S;
@@ -509,22 +528,34 @@ cudaError_t launch_apply_mask_dense(const BatchDev &b, int K, const uint32_t *bi
 }
 
 cudaError_t launch_synth_fp32(const BatchDev &b, int K, int s, const float *d, const float *z,
-                              const uint32_t *bits, const float *x, float *out, cudaStream_t st) {
+                              const uint32_t *bits, const float *x, float *out, cudaStream_t st,
+                              int ksplit, float *partial) {
   if (b.n_tiles == 0) return cudaSuccess;
-  return dispatch_s(s, [&](auto SC) {
+  if (ksplit < 1 || partial == nullptr) ksplit = 1;
+  const int kspan = ((K + ksplit - 1) / ksplit + 3) / 4 * 4;
+  ksplit = (K + kspan - 1) / kspan;
+  cudaError_t e = dispatch_s(s, [&](auto SC) {
     constexpr int S = decltype(SC)::value;
-    synth_fp32_kernel<S, 4><<<b.n_tiles, 128, 0, st>>>(b, K, d, z, bits, x, out);
+    dim3 grid(b.n_tiles, ksplit);
+    synth_fp32_kernel<S, 4><<<grid, 128, 0, st>>>(b, K, kspan, d, z, bits, x,
+                                                   ksplit > 1 ? partial : out);
     return cudaGetLastError();
   });
+  if (e != cudaSuccess || ksplit == 1) return e;
+  sum_split_kernel<<<grid_for(b.total_px, 256, 152 * 8), 256, 0, st>>>(partial, ksplit, b.total_px,
+                                                                         x, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_fp32(const BatchDev &b, int K, int s, const float *d, const float *r,
                                 const uint32_t *bits, int mode, const StepParams *prm,
-                                float *zg, cudaStream_t st) {
+                                float *zg, cudaStream_t st, int ksplit) {
   if (b.n_tiles == 0) return cudaSuccess;
+  ksplit = std::max(1, std::min(ksplit, (K + 31) / 32));
   return dispatch_s(s, [&](auto SC) {
     constexpr int S = decltype(SC)::value;
-    adjoint_fp32_kernel<S><<<b.n_tiles, 128, 0, st>>>(b, K, d, r, bits, mode, prm, zg);
+    dim3 grid(b.n_tiles, ksplit);
+    adjoint_fp32_kernel<S><<<grid, 128, 0, st>>>(b, K, d, r, bits, mode, prm, zg);
     return cudaGetLastError();
   });
 }

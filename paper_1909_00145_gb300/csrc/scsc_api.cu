@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -71,7 +72,7 @@ struct scsc_ctx {
   std::string err;
   BatchCache batch, domain;     // the call's batch; the step-size domain
   int domainH = -1, domainW = -1;
-  DevBuf bits, r, pix2, prm, scal, partials, gpart, gsum, pu, pw, pcodes, flag;
+  DevBuf bits, r, pix2, prm, scal, partials, gpart, gsum, pu, pw, pcodes, psplit, flag;
   // tensor path
   TcWorkspace tc;
   // online surrogates
@@ -200,12 +201,16 @@ scsc_status build_mask(scsc_ctx *ctx, uint64_t t) {
 }
 
 // Operator D D^T on the step-size domain: u (pixels) -> w (pixels).
+// A single image gives few 32x32 tiles, so the filters are split over blocks
+// until the launch has about two blocks per SM.
 scsc_status apply_ddt(scsc_ctx *ctx, const float *d, const float *u, float *w) {
   const BatchDev &b = ctx->domain.view;
+  const int ksplit = std::max(1, std::min((304 + b.n_tiles - 1) / b.n_tiles, (ctx->cfg.K + 31) / 32));
+  CK(ctx->psplit.ensure((size_t)ksplit * b.total_px * 4));
   CK(launch_adjoint_fp32(b, ctx->cfg.K, ctx->cfg.s, d, u, nullptr, 0, nullptr,
-                         ctx->pcodes.as<float>(), ctx->stream));
+                         ctx->pcodes.as<float>(), ctx->stream, ksplit));
   CK(launch_synth_fp32(b, ctx->cfg.K, ctx->cfg.s, d, ctx->pcodes.as<float>(), nullptr, nullptr, w,
-                       ctx->stream));
+                       ctx->stream, ksplit, ctx->psplit.as<float>()));
   return SCSC_OK;
 }
 
@@ -333,7 +338,8 @@ scsc_status scsc_destroy(scsc_ctx *ctx) {
   if (!ctx) return SCSC_OK;
   cudaStreamSynchronize(ctx->stream);
   for (DevBuf *b : {&ctx->bits, &ctx->r, &ctx->pix2, &ctx->prm, &ctx->scal, &ctx->partials,
-                    &ctx->gpart, &ctx->gsum, &ctx->pu, &ctx->pw, &ctx->pcodes, &ctx->flag,
+                    &ctx->gpart, &ctx->gsum, &ctx->pu, &ctx->pw, &ctx->pcodes, &ctx->psplit,
+                    &ctx->flag,
                     &ctx->C, &ctx->B, &ctx->Cd, &ctx->batch.dev, &ctx->domain.dev})
     b->release();
   for (BatchCache *bc : {&ctx->batch, &ctx->domain}) {

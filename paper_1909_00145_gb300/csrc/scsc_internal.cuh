@@ -73,11 +73,14 @@ cudaError_t launch_mask_bits(const BatchDev &b, int K, uint64_t seed, uint64_t t
                              uint32_t *bits, cudaStream_t st);
 cudaError_t launch_apply_mask_dense(const BatchDev &b, int K, const uint32_t *bits, float *z,
                                     cudaStream_t st);
+// ksplit > 1 splits the filters over ksplit blocks per tile (small domains);
+// the synthesis then needs `partial` of ksplit * total_px floats.
 cudaError_t launch_synth_fp32(const BatchDev &b, int K, int s, const float *d, const float *z,
-                              const uint32_t *bits, const float *x, float *out, cudaStream_t st);
+                              const uint32_t *bits, const float *x, float *out, cudaStream_t st,
+                              int ksplit = 1, float *partial = nullptr);
 cudaError_t launch_adjoint_fp32(const BatchDev &b, int K, int s, const float *d, const float *r,
                                 const uint32_t *bits, int mode, const StepParams *prm,
-                                float *z_or_g, cudaStream_t st);
+                                float *z_or_g, cudaStream_t st, int ksplit = 1);
 cudaError_t launch_filter_grad_fp32(const BatchDev &b, int K, int s, const float *r,
                                     const float *z, const uint32_t *bits, float *partial,
                                     int n_groups, cudaStream_t st);
