@@ -202,6 +202,10 @@ def main():
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--per-image", action="store_true",
+                    help="plain path: launch the kernels once per image (batched-launch baseline)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="tensor path: launch iterations directly instead of replaying a graph")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -229,7 +233,9 @@ def main():
     x = torch.from_numpy(x_np).cuda()
     d = torch.from_numpy(d_np).cuda().contiguous()
     z = torch.zeros(npx * K, dtype=torch.float32, device="cuda")
-    ctx = scsc.Context(K, 11, 1.0, wl["p"], seed=0, prec=args.prec, stream=stream)
+    flags = (scsc.SCSC_FLAG_PER_IMAGE if args.per_image else 0) | \
+        (scsc.SCSC_FLAG_NO_GRAPH if args.no_graph else 0)
+    ctx = scsc.Context(K, 11, 1.0, wl["p"], seed=0, prec=args.prec, stream=stream, flags=flags)
 
     def barrier():
         if world > 1:
@@ -239,7 +245,7 @@ def main():
         for i in range(args.warmup):
             ctx.code_step(batch, x, d, z, 1 + i, n_iters)
         ctx.sync()
-        scsc.scsc_diag_profile(ctx, True)
+        z_warm = z.clone()
         sampler = ClockSampler(local)
         barrier()
         torch.cuda.synchronize()
@@ -263,14 +269,38 @@ def main():
     units = npx * K * n_iters * args.steps * world
     value = units / (ms / 1e3) / 1e9
 
-    # dominant kernel and its roofline
+    # per-kernel device times: the same steps again with CUDA events around
+    # every launch of the library (direct launches, no graph replay)
     kt = {}
-    for name in ["synth_tc", "adj_tc", "finalize_r", "synth_fp32", "adjoint_fp32", "pack",
-                 "unpack", "power", "mask"]:
-        tot, n = scsc.scsc_diag_kernel_time(ctx, name)
-        if n:
-            kt[name] = (tot, n)
-    scsc.scsc_diag_profile(ctx, False)
+    prof_steps = min(args.steps, 3)
+    with torch.cuda.stream(stream):
+        scsc.scsc_diag_profile(ctx, True)
+        for i in range(prof_steps):
+            ctx.code_step(batch, x, d, z, 100 + i, n_iters)
+        ctx.sync()
+        for name in ["synth_tc", "adj_tc", "finalize_r", "synth_fp32", "adjoint_fp32", "pack",
+                     "unpack", "power", "mask"]:
+            tot, n = scsc.scsc_diag_kernel_time(ctx, name)
+            if n:
+                kt[name] = (tot, n)
+        scsc.scsc_diag_profile(ctx, False)
+
+    # accuracy of this path against the plain FP32 path: one code step from
+    # the same warm state, relative difference of the Eq. 1 objectives
+    rel_err = None
+    if args.prec != "fp32":
+        with torch.cuda.stream(stream):
+            ref = scsc.Context(K, 11, 1.0, wl["p"], seed=0, prec="fp32", stream=stream)
+            za, zb = z_warm.clone(), z_warm.clone()
+            ctx.code_step(batch, x, d, za, 500, n_iters)
+            ref.code_step(batch, x, d, zb, 500, n_iters)
+            fa = ctx.objective(batch, x, za, d)
+            fb = ref.objective(batch, x, zb, d)
+            rel_err = abs(fa - fb) / abs(fb)
+            ref.close()
+            del za, zb
+    del z_warm
+
     dom = max(kt, key=lambda k: kt[k][0]) if kt else None
     hbm, bf16, bf16s, src = peaks()
     sampled = float(wl["p"][0]) / wl["p"][1] * npx * K  # expected sampled coordinates
@@ -324,10 +354,13 @@ def main():
                "config": {"workload": wl["desc"], "images_per_gpu": int(len(H)),
                           "pixels_per_gpu": npx, "K": K, "p": f"{wl['p'][0]}/{wl['p'][1]}",
                           "n_iters": n_iters, "path": args.prec,
+                          "launches": "per image" if args.per_image else "batched",
+                          "graph": not args.no_graph,
                           "l2": "inputs larger than L2 (dense codes %.2f GB)" % (npx * K * 4 / 1e9)},
                "clocks": clocks,
                "roofline": roof,
-               "kernels_ms_per_step": {k: v[0] / args.steps for k, v in kt.items()},
+               "kernels_ms_per_step": {k: v[0] / prof_steps for k, v in kt.items()},
+               "rel_obj_err_vs_fp32": rel_err,
                "e2e": {"value": e2e_val, "unit": "Gpix*filter/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h},
                "gpu_launches": launches_per_step(args.prec, n_iters) * args.steps}

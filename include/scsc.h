@@ -65,7 +65,18 @@ typedef struct {
   uint64_t seed;     /* seed of the counter-based subsampling hash             */
   scsc_precision prec;
   double step;       /* > 0: fixed code step alpha; 0: alpha = 1 / L_z          */
+  uint32_t flags;    /* OR of SCSC_FLAG_* below; 0 = defaults                   */
 } scsc_config;
+
+/* SCSC_FLAG_PER_IMAGE: plain path launches its kernels once per image
+ *   instead of once over the whole batch (the baseline of batched launches).
+ * SCSC_FLAG_NO_GRAPH: tensor path launches every iteration directly instead
+ *   of replaying a captured CUDA graph of the iteration loop.
+ * SCSC_FLAG_NO_AUTOTUNE: tensor path skips the variant timing on the first
+ *   call for a shape and uses the pipelined kernels when they apply. */
+#define SCSC_FLAG_PER_IMAGE 1u
+#define SCSC_FLAG_NO_GRAPH 2u
+#define SCSC_FLAG_NO_AUTOTUNE 4u
 
 typedef struct {   /* host arrays, n_images entries each */
   int n_images;

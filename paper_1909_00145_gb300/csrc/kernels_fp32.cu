@@ -21,6 +21,7 @@ struct TileCoord {
 };
 
 __device__ __forceinline__ TileCoord tile_coord(const BatchDev &b, int tile) {
+  tile += b.tile_base;
   TileCoord c;
   c.n = upper_index(b.tile0, b.n, tile);
   c.H = b.H[c.n];

@@ -639,6 +639,7 @@ cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint32_t
 cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
                         const uint64_t *seg_base, float *packed, const uint4 *badj, const float *r,
                         const StepParams *prm, int *err, int grid, cudaStream_t st);
+cudaError_t prepare_pipe(int K, int s, int max_smem);
 
 int *tc_error_word(TcWorkspace &ws) {
   if (ensure(ws.err, sizeof(int)) != cudaSuccess) return nullptr;
@@ -648,6 +649,8 @@ int *tc_error_word(TcWorkspace &ws) {
 const char *tc_last_error(const TcWorkspace &ws) { return ws.last_error.c_str(); }
 
 void tc_release(TcWorkspace &ws) {
+  if (ws.graph_exec) cudaGraphExecDestroy(ws.graph_exec);
+  ws.graph_exec = nullptr;
   for (TcWorkspace::Buf *b : {&ws.item0, &ws.seg_count, &ws.seg_base, &ws.scan_blocks, &ws.packed,
                               &ws.xcore, &ws.spill, &ws.r, &ws.badj, &ws.bsyn, &ws.err}) {
     if (b->p) cudaFree(b->p);
@@ -733,61 +736,139 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
     TRY(cudaGetDevice(&dev));
     TRY(cudaDeviceGetAttribute(&ws.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   }
-  if (tc_pipe_supported(K, s, ws.max_smem)) {
-    const int grid = std::min(Q, ws.sm_count);
-    const int fin_grid = (int)std::min<int64_t>((b.total_px + 255) / 256, 152 * 16);
-    for (int it = 0; it < n_iters; ++it) {
-      int p1 = ws.prof ? ws.prof->begin(KID_SYNTH_TC, st) : -1;
-      TRY(launch_syn2(im, K, s, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.bsyn),
-                      as<float>(ws.xcore), as<float>(ws.spill), as<int>(ws.err), grid,
-                      ws.max_smem, st));
-      if (ws.prof) ws.prof->end(p1, st);
-      int p2 = ws.prof ? ws.prof->begin(KID_FINALIZE, st) : -1;
-      finalize_r_kernel<<<fin_grid, 256, 0, st>>>(b, im, C, as<float>(ws.xcore),
-                                                   as<float>(ws.spill), x, as<float>(ws.r));
-      TRY(cudaGetLastError());
-      if (ws.prof) ws.prof->end(p2, st);
-      int p3 = ws.prof ? ws.prof->begin(KID_ADJ_TC, st) : -1;
-      TRY(launch_adj2(im, K, s, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.badj),
-                      as<float>(ws.r), prm, as<int>(ws.err), grid, st));
-      if (ws.prof) ws.prof->end(p3, st);
-    }
-  } else TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
+  const bool pipe_ok = tc_pipe_supported(K, s, ws.max_smem);
+  const int fin_grid = (int)std::min<int64_t>((b.total_px + 255) / 256, 152 * 16);
+  // launch geometry of the single-stage kernels (several CTAs per SM)
+  int grid_s1 = 1, grid_a1 = 1;
+  size_t smem_s1 = 0, smem_a1 = 0;
+  TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
-    const size_t smem_syn = SynthSmem<S>::total(Kp), smem_adj = AdjSmem<S>::total(Kp);
-    auto ks = synth_tc_kernel<S>;
-    auto ka = adj_tc_kernel<S>;
-    TRY(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_syn));
-    TRY(cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_adj));
+    smem_s1 = SynthSmem<S>::total(Kp);
+    smem_a1 = AdjSmem<S>::total(Kp);
+    TRY(cudaFuncSetAttribute(synth_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_s1));
+    TRY(cudaFuncSetAttribute(adj_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_a1));
     int occ_s = 0, occ_a = 0;
-    TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, ks, kThreads, smem_syn));
-    TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, ka, kThreads, smem_adj));
+    TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, synth_tc_kernel<S>, kThreads,
+                                                      smem_s1));
+    TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_a, adj_tc_kernel<S>, kThreads,
+                                                      smem_a1));
     occ_s = std::max(1, std::min(occ_s, 512 / 256));
     occ_a = std::max(1, std::min(occ_a, 512 / tmem_cols_for(Kp)));
-    const int grid_s = std::min(Q, ws.sm_count * occ_s);
-    const int grid_a = std::min(Q, ws.sm_count * occ_a);
-    const int fin_grid = (int)std::min<int64_t>((b.total_px + 255) / 256, 152 * 16);
-    for (int it = 0; it < n_iters; ++it) {
-      int p1 = ws.prof ? ws.prof->begin(KID_SYNTH_TC, st) : -1;
-      ks<<<grid_s, kThreads, smem_syn, st>>>(im, K, Kp, KW, bits, seg_base, as<float>(ws.packed),
-                                            as<uint4>(ws.bsyn), as<float>(ws.xcore),
-                                            as<float>(ws.spill), as<int>(ws.err));
-      TRY(cudaGetLastError());
-      if (ws.prof) ws.prof->end(p1, st);
-      int p2 = ws.prof ? ws.prof->begin(KID_FINALIZE, st) : -1;
-      finalize_r_kernel<<<fin_grid, 256, 0, st>>>(b, im, C, as<float>(ws.xcore),
-                                                   as<float>(ws.spill), x, as<float>(ws.r));
-      TRY(cudaGetLastError());
-      if (ws.prof) ws.prof->end(p2, st);
-      int p3 = ws.prof ? ws.prof->begin(KID_ADJ_TC, st) : -1;
-      ka<<<grid_a, kThreads, smem_adj, st>>>(im, K, Kp, KW, bits, seg_base, as<float>(ws.packed),
-                                            as<uint4>(ws.badj), as<float>(ws.r), prm,
-                                            as<int>(ws.err));
-      TRY(cudaGetLastError());
-      if (ws.prof) ws.prof->end(p3, st);
-    }
+    grid_s1 = std::min(Q, ws.sm_count * occ_s);
+    grid_a1 = std::min(Q, ws.sm_count * occ_a);
     return cudaSuccess;
   }));
+  if (pipe_ok) TRY(prepare_pipe(K, s, ws.max_smem));
+  const int grid2 = std::min(Q, ws.sm_count);
+
+  // One proximal-gradient iteration with kernel variant v (0 single-stage,
+  // 1 pipelined): synthesis, residual, adjoint + prox.
+  auto iteration = [&](int v) -> cudaError_t {
+    int p1 = ws.prof ? ws.prof->begin(KID_SYNTH_TC, st) : -1;
+    if (v == 1) {
+      TRY(launch_syn2(im, K, s, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.bsyn),
+                      as<float>(ws.xcore), as<float>(ws.spill), as<int>(ws.err), grid2,
+                      ws.max_smem, st));
+    } else {
+      TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
+        constexpr int S = decltype(SC)::value;
+        synth_tc_kernel<S><<<grid_s1, kThreads, smem_s1, st>>>(
+            im, K, Kp, KW, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.bsyn),
+            as<float>(ws.xcore), as<float>(ws.spill), as<int>(ws.err));
+        return cudaGetLastError();
+      }));
+    }
+    if (ws.prof) ws.prof->end(p1, st);
+    int p2 = ws.prof ? ws.prof->begin(KID_FINALIZE, st) : -1;
+    finalize_r_kernel<<<fin_grid, 256, 0, st>>>(b, im, C, as<float>(ws.xcore), as<float>(ws.spill),
+                                                 x, as<float>(ws.r));
+    TRY(cudaGetLastError());
+    if (ws.prof) ws.prof->end(p2, st);
+    int p3 = ws.prof ? ws.prof->begin(KID_ADJ_TC, st) : -1;
+    if (v == 1) {
+      TRY(launch_adj2(im, K, s, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.badj),
+                      as<float>(ws.r), prm, as<int>(ws.err), grid2, st));
+    } else {
+      TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
+        constexpr int S = decltype(SC)::value;
+        adj_tc_kernel<S><<<grid_a1, kThreads, smem_a1, st>>>(
+            im, K, Kp, KW, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.badj),
+            as<float>(ws.r), prm, as<int>(ws.err));
+        return cudaGetLastError();
+      }));
+    }
+    if (ws.prof) ws.prof->end(p3, st);
+    return cudaSuccess;
+  };
+
+  // Autotuner: the first call for a (device, K, s, shape class) runs its
+  // first two iterations once with each variant, times them with events and
+  // keeps the faster one for every later call with the same key.
+  int variant = pipe_ok ? 1 : 0;
+  int done = 0;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  TRY(cudaStreamIsCapturing(st, &cap));
+  const bool user_capture = cap != cudaStreamCaptureStatusNone;
+  if (pipe_ok && ws.autotune) {
+    int dev = 0;
+    TRY(cudaGetDevice(&dev));
+    int qclass = 0;
+    while ((1 << (qclass + 1)) <= Q) ++qclass;
+    const TuneKey key{dev, K, s, qclass};
+    auto hit = ws.tune.find(key);
+    if (hit != ws.tune.end()) {
+      variant = hit->second;
+    } else if (n_iters >= 2 && !user_capture) {
+      cudaEvent_t ev[4];
+      for (auto &e : ev) TRY(cudaEventCreate(&e));
+      float ms[2] = {0.f, 0.f};
+      cudaError_t err = cudaSuccess;
+      for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
+        err = cudaEventRecord(ev[2 * v], st);
+        if (err == cudaSuccess) err = iteration(v);
+        if (err == cudaSuccess) err = cudaEventRecord(ev[2 * v + 1], st);
+      }
+      if (err == cudaSuccess) err = cudaEventSynchronize(ev[3]);
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms[0], ev[0], ev[1]);
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&ms[1], ev[2], ev[3]);
+      for (auto &e : ev) cudaEventDestroy(e);
+      TRY(err);
+      variant = ms[1] <= ms[0] ? 1 : 0;
+      ws.tune[key] = variant;
+      ws.tune_ms[key] = std::make_pair(ms[0], ms[1]);
+      done = 2;
+    }
+  }
+
+  // Remaining iterations: replayed from a CUDA graph captured once per
+  // (buffers, shape, variant, count), or launched directly when profiling,
+  // when the caller is itself capturing, or on the legacy default stream.
+  const int rem = n_iters - done;
+  const bool use_graph = ws.graphs && rem > 0 && st != nullptr && !user_capture &&
+                         !(ws.prof && ws.prof->on);
+  if (use_graph) {
+    const GraphKey gk{bits, seg_base, ws.packed.p, ws.bsyn.p, ws.badj.p, ws.xcore.p, ws.spill.p,
+                      ws.r.p, ws.err.p, x, prm, ws.item0.p, b.off, K, s, Q, variant, rem};
+    if (!ws.graph_exec || std::memcmp(&gk, &ws.graph_key, sizeof gk) != 0) {
+      if (ws.graph_exec) cudaGraphExecDestroy(ws.graph_exec);
+      ws.graph_exec = nullptr;
+      cudaGraph_t g = nullptr;
+      TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      cudaError_t err = cudaSuccess;
+      for (int it = 0; it < rem && err == cudaSuccess; ++it) err = iteration(variant);
+      cudaError_t e2 = cudaStreamEndCapture(st, &g);
+      if (err == cudaSuccess) err = e2;
+      if (err == cudaSuccess) err = cudaGraphInstantiate(&ws.graph_exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      TRY(err);
+      ws.graph_key = gk;
+    }
+    TRY(cudaGraphLaunch(ws.graph_exec, st));
+  } else {
+    for (int it = 0; it < rem; ++it) TRY(iteration(variant));
+  }
   // Eq. 4: dense codes, zero off the sampled set
   int pu = ws.prof ? ws.prof->begin(KID_UNPACK, st) : -1;
   pack_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, as<float>(ws.packed), z, 1);

@@ -805,6 +805,21 @@ bool tc_pipe_supported(int K, int s, int max_smem) {
   return need > 0 && need <= (size_t)max_smem;
 }
 
+// Shared-memory attributes of both pipelined kernels (set once, outside any
+// stream capture).
+cudaError_t prepare_pipe(int K, int s, int max_smem) {
+  const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
+  return dispatch_s(s, [&](auto SC) -> cudaError_t {
+    constexpr int S = decltype(SC)::value;
+    int nst = Syn2<S>::total(Kp, KW, 2) <= (size_t)max_smem ? 2 : 1;
+    cudaError_t e = cudaFuncSetAttribute(syn2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)Syn2<S>::total(Kp, KW, nst));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(adj2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)Adj2<S>::total(Kp, KW));
+  });
+}
+
 cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
                         const uint64_t *seg_base, const float *packed, const uint4 *bsyn,
                         float *xcore, float *spill, int *err, int grid, int max_smem,
@@ -814,9 +829,6 @@ cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint32_t
     constexpr int S = decltype(SC)::value;
     int nst = Syn2<S>::total(Kp, KW, 2) <= (size_t)max_smem ? 2 : 1;
     const size_t smem = Syn2<S>::total(Kp, KW, nst);
-    cudaError_t e = cudaFuncSetAttribute(syn2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     syn2_kernel<S><<<grid, 256, smem, st>>>(im, K, Kp, KW, nst, bits, seg_base, packed, bsyn,
                                             xcore, spill, err);
     return cudaGetLastError();
@@ -830,9 +842,6 @@ cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t
   return dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
     const size_t smem = Adj2<S>::total(Kp, KW);
-    cudaError_t e = cudaFuncSetAttribute(adj2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     adj2_kernel<S><<<grid, 256, smem, st>>>(im, K, Kp, KW, bits, seg_base, packed, badj, r, prm,
                                             err);
     return cudaGetLastError();

@@ -173,9 +173,28 @@ scsc_status upload_batch(scsc_ctx *ctx, BatchCache &bc, int n, const int64_t *of
   bc.view.tile0 = reinterpret_cast<const int *>(d + (n + 1) * 8 + n * 8 + n * 8);
   bc.view.total_px = pos;
   bc.view.n_tiles = (int)tiles;
+  bc.view.tile_base = 0;
   bc.maxH = mh;
   bc.maxW = mw;
   return SCSC_OK;
+}
+
+// Device view of image i alone (pointers into the batch's descriptor).
+BatchDev image_view(const BatchCache &bc, int i) {
+  const int n = bc.view.n;
+  const int64_t *off = reinterpret_cast<const int64_t *>(bc.host.data());
+  const int *t0 = reinterpret_cast<const int *>(bc.host.data() + (n + 1) * 8 + n * 8 + n * 8);
+  BatchDev v = bc.view;
+  v.n = 1;
+  v.off = bc.view.off + i;
+  v.ids = bc.view.ids + i;
+  v.H = bc.view.H + i;
+  v.W = bc.view.W + i;
+  v.tile0 = bc.view.tile0 + i;
+  v.total_px = off[i + 1] - off[i];
+  v.n_tiles = t0[i + 1] - t0[i];
+  v.tile_base = t0[i];
+  return v;
 }
 
 scsc_status stage_batch(scsc_ctx *ctx, const scsc_batch *b) {
@@ -306,6 +325,8 @@ scsc_status check_cfg(scsc_ctx *ctx, const scsc_config *c) {
     return fail(ctx, SCSC_EINVAL, "step must be finite and >= 0");
   if (c->prec != SCSC_FP32 && c->prec != SCSC_BF16)
     return fail(ctx, SCSC_EINVAL, "unknown precision %d", (int)c->prec);
+  if (c->flags & ~(SCSC_FLAG_PER_IMAGE | SCSC_FLAG_NO_GRAPH | SCSC_FLAG_NO_AUTOTUNE))
+    return fail(ctx, SCSC_EINVAL, "unknown flags 0x%x", c->flags);
   return SCSC_OK;
 }
 
@@ -325,6 +346,8 @@ scsc_status scsc_create(const scsc_config *cfg, void *cuda_stream, scsc_ctx **ou
   if (!c) return SCSC_ENOMEM;
   c->cfg = *cfg;
   c->tc.prof = &c->prof;
+  c->tc.graphs = (cfg->flags & SCSC_FLAG_NO_GRAPH) == 0;
+  c->tc.autotune = (cfg->flags & SCSC_FLAG_NO_AUTOTUNE) == 0;
   c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     delete c;
@@ -408,14 +431,25 @@ scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
   // Plain FP32 path.  Eq. 4 warm start: unsampled codes are zero.
   CK(launch_apply_mask_dense(b, K, ctx->bits.as<uint32_t>(), z_dev, st));
   CK(ctx->r.ensure((size_t)b.total_px * 4));
+  // views to launch over: the whole batch, or each image on its own
+  std::vector<BatchDev> views;
+  if (ctx->cfg.flags & SCSC_FLAG_PER_IMAGE) {
+    for (int i = 0; i < b.n; ++i) views.push_back(image_view(ctx->batch, i));
+  } else {
+    views.push_back(b);
+  }
   for (int it = 0; it < n_iters; ++it) {
-    int p1 = ctx->prof.begin(KID_SYNTH_FP32, st);
-    CK(launch_synth_fp32(b, K, s, d_dev, z_dev, nullptr, x_dev, ctx->r.as<float>(), st));
-    ctx->prof.end(p1, st);
-    int p2 = ctx->prof.begin(KID_ADJ_FP32, st);
-    CK(launch_adjoint_fp32(b, K, s, d_dev, ctx->r.as<float>(), ctx->bits.as<uint32_t>(), 1, prm,
-                           z_dev, st));
-    ctx->prof.end(p2, st);
+    for (const BatchDev &v : views) {
+      int p1 = ctx->prof.begin(KID_SYNTH_FP32, st);
+      CK(launch_synth_fp32(v, K, s, d_dev, z_dev, nullptr, x_dev, ctx->r.as<float>(), st));
+      ctx->prof.end(p1, st);
+    }
+    for (const BatchDev &v : views) {
+      int p2 = ctx->prof.begin(KID_ADJ_FP32, st);
+      CK(launch_adjoint_fp32(v, K, s, d_dev, ctx->r.as<float>(), ctx->bits.as<uint32_t>(), 1,
+                             prm, z_dev, st));
+      ctx->prof.end(p2, st);
+    }
   }
   return SCSC_OK;
 }

@@ -23,6 +23,7 @@ struct BatchDev {
   const int *tile0;     // [n + 1] first 32x32 tile of each image
   int64_t total_px;
   int n_tiles;          // tile0[n]
+  int tile_base;        // global index of this view's first tile (sub-batches)
 };
 
 // Parameters of the proximal step, read by the kernels from device memory so

@@ -1,13 +1,31 @@
 // scsc_tc.cuh -- the tensor-core (tcgen05, BF16 operands, FP32 accumulation)
 // code-update path and the small helpers shared with the plain path.
 #pragma once
+#include <map>
 #include <string>
+#include <tuple>
+#include <utility>
 #include <vector>
 
 #include "profiler.cuh"
 #include "scsc_internal.cuh"
 
 namespace scsc {
+
+// Autotuner key: device, K, s, log2 of the number of row items.
+struct TuneKey {
+  int dev, K, s, qclass;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(dev, K, s, qclass) < std::tie(o.dev, o.K, o.s, o.qclass);
+  }
+};
+
+// Everything a captured iteration graph depends on.
+struct GraphKey {
+  const void *bits, *seg_base, *packed, *bsyn, *badj, *xcore, *spill, *r, *err, *x, *prm, *item0,
+      *off;
+  int K, s, Q, variant, iters;
+};
 
 // Workspace of the tensor path, owned by the context.
 struct TcWorkspace {
@@ -22,6 +40,11 @@ struct TcWorkspace {
   int sm_count = 0;
   int max_smem = 0;
   Profiler *prof = nullptr;  // the owning context's profiler
+  bool autotune = true, graphs = true;
+  std::map<TuneKey, int> tune;                       // chosen variant per key
+  std::map<TuneKey, std::pair<float, float>> tune_ms;  // timings that chose it
+  cudaGraphExec_t graph_exec = nullptr;
+  GraphKey graph_key{};
   std::string last_error;
 };
 

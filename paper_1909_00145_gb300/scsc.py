@@ -26,11 +26,13 @@ STATUS_NAMES = ["SCSC_OK", "SCSC_EINVAL", "SCSC_ENOMEM", "SCSC_ECUDA", "SCSC_ETI
                 "SCSC_ENONFINITE", "SCSC_EUNSUPPORTED"]
 SCSC_FP32, SCSC_BF16 = 0, 1
 SCSC_DICT_BATCH, SCSC_DICT_ONLINE = 0, 1
+SCSC_FLAG_PER_IMAGE, SCSC_FLAG_NO_GRAPH, SCSC_FLAG_NO_AUTOTUNE = 1, 2, 4
 
 
 class scsc_config(ctypes.Structure):
     _fields_ = [("K", c_int), ("s", c_int), ("lambda_", c_double), ("p_num", c_u32),
-                ("p_den", c_u32), ("seed", c_u64), ("prec", c_int), ("step", c_double)]
+                ("p_den", c_u32), ("seed", c_u64), ("prec", c_int), ("step", c_double),
+                ("flags", c_u32)]
 
 
 class scsc_batch(ctypes.Structure):
@@ -156,13 +158,13 @@ class Context:
     """An scsc_ctx bound to the current device and a CUDA stream."""
 
     def __init__(self, K: int, s: int = 11, lam: float = 1.0, p=(1, 1), seed: int = 0,
-                 prec: str = "fp32", step: float = 0.0, stream=None):
+                 prec: str = "fp32", step: float = 0.0, stream=None, flags: int = 0):
         self.K, self.s, self.lam = int(K), int(s), float(lam)
         self.p = (int(p[0]), int(p[1]))
         self.seed = int(seed)
         self.prec = {"fp32": SCSC_FP32, "bf16": SCSC_BF16}[prec]
         self.cfg = scsc_config(self.K, self.s, self.lam, self.p[0], self.p[1], self.seed,
-                               self.prec, float(step))
+                               self.prec, float(step), int(flags))
         self.stream = stream
         self.handle = c_void_p()
         _check(lib().scsc_create(ctypes.byref(self.cfg), c_void_p(_stream_handle(stream)),
@@ -207,8 +209,8 @@ class Context:
 
 # ------------------------------------------------------------------ entry points
 
-def scsc_create(K, s=11, lam=1.0, p=(1, 1), seed=0, prec="fp32", step=0.0, stream=None):
-    return Context(K, s, lam, p, seed, prec, step, stream)
+def scsc_create(K, s=11, lam=1.0, p=(1, 1), seed=0, prec="fp32", step=0.0, stream=None, flags=0):
+    return Context(K, s, lam, p, seed, prec, step, stream, flags)
 
 
 def scsc_destroy(ctx: Context) -> None:
@@ -277,7 +279,7 @@ def scsc_objective_noalloc(K: int, s: int, lam: float, n_images: int, H: int, W:
                            out, stream=None) -> None:
     """Eq. 1 for equal-size images into the device double `out`, using only the
     library's built-in scratch (no device allocation)."""
-    cfg = scsc_config(int(K), int(s), float(lam), 1, 1, 0, SCSC_FP32, 0.0)
+    cfg = scsc_config(int(K), int(s), float(lam), 1, 1, 0, SCSC_FP32, 0.0, 0)
     _check(lib().scsc_objective_noalloc(ctypes.byref(cfg), n_images, H, W, _ptr(x), _ptr(z),
                                         _ptr(d), _ptr(out), c_void_p(_stream_handle(stream))),
            None, "scsc_objective_noalloc")

@@ -45,12 +45,12 @@ def test_library_is_built_for_sm103a():
 def test_config_validation_happens_on_the_host():
     L = scsc.lib()
     bad = [dict(K=0), dict(K=600), dict(s=4), dict(s=13), dict(lam=0.0), dict(p=(3, 2)),
-           dict(p=(1, 0)), dict(step=-1.0)]
+           dict(p=(1, 0)), dict(step=-1.0), dict(flags=8), dict(prec=2)]
     for kw in bad:
-        args = dict(K=16, s=11, lam=1.0, p=(1, 2), step=0.0)
+        args = dict(K=16, s=11, lam=1.0, p=(1, 2), step=0.0, flags=0, prec=0)
         args.update(kw)
         cfg = scsc.scsc_config(args["K"], args["s"], args["lam"], args["p"][0], args["p"][1], 0,
-                               0, args["step"])
+                               args["prec"], args["step"], args["flags"])
         h = ctypes.c_void_p()
         assert L.scsc_create(ctypes.byref(cfg), None, ctypes.byref(h)) == scsc.SCSC_EINVAL, kw
         assert not h
@@ -67,4 +67,4 @@ def test_batch_descriptor_layout():
     b = scsc.Batch([3, 5], [4, 2], ids=[7, 9])
     assert list(b.offsets) == [0, 12]
     assert b.total_pixels == 22
-    assert ctypes.sizeof(scsc.scsc_config) == 48
+    assert ctypes.sizeof(scsc.scsc_config) == 56
