@@ -204,6 +204,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--per-image", action="store_true",
                     help="plain path: launch the kernels once per image (batched-launch baseline)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="tensor path: always use the pipelined kernels (for profiler captures)")
     ap.add_argument("--no-graph", action="store_true",
                     help="tensor path: launch iterations directly instead of replaying a graph")
     args = ap.parse_args()
@@ -234,7 +236,8 @@ def main():
     d = torch.from_numpy(d_np).cuda().contiguous()
     z = torch.zeros(npx * K, dtype=torch.float32, device="cuda")
     flags = (scsc.SCSC_FLAG_PER_IMAGE if args.per_image else 0) | \
-        (scsc.SCSC_FLAG_NO_GRAPH if args.no_graph else 0)
+        (scsc.SCSC_FLAG_NO_GRAPH if args.no_graph else 0) | \
+        (scsc.SCSC_FLAG_NO_AUTOTUNE if args.no_autotune else 0)
     ctx = scsc.Context(K, 11, 1.0, wl["p"], seed=0, prec=args.prec, stream=stream, flags=flags)
 
     def barrier():

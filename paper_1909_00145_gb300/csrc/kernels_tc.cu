@@ -130,33 +130,42 @@ __global__ void scan_add_kernel(uint64_t *out, int n, const uint64_t *block_sums
 
 // mode 0: packed <- z on the sampled set (warm start)
 // mode 1: z <- packed on the sampled set, 0 elsewhere (Eq. 4)
+// One block per item.  The item's dense codes are one contiguous block of
+// npx * K floats, walked linearly by the block (coalesced); each element
+// finds its packed slot from per-pixel chunk offsets staged in shared memory.
+constexpr int kMaxChunks = 16;  // K <= 256
 __global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int KW, int NC,
                                                         const uint32_t *bits,
                                                         const uint64_t *seg_base, float *packed,
                                                         float *z, int mode) {
   __shared__ int sh[4];
+  __shared__ uint16_t s_m[kMaxChunks][kStrip];
+  __shared__ uint32_t s_off[kMaxChunks][kStrip];
   const int q = blockIdx.x;
   const Item it = item_of(im, q);
   const int col = it.js * kStrip + threadIdx.x;
-  const bool inside = col < it.W;
-  const int64_t pix = it.base + (int64_t)it.a * it.W + col;
+  const uint64_t item_base = seg_base[(int64_t)q * NC];
   for (int c = 0; c < NC; ++c) {
     uint32_t m = chunk_mask(bits, KW, it, it.a, col, c);
     int total;
     int off = scan128(__popc(m), sh, total);
-    float *seg = packed + seg_base[(int64_t)q * NC + c] + off;
-    int rank = 0;
-#pragma unroll
-    for (int e = 0; e < 16; ++e) {
-      int k = 16 * c + e;
-      if (!inside || k >= K) continue;
-      if ((m >> e) & 1u) {
-        if (mode == 0) seg[rank] = z[pix * K + k];
-        else z[pix * K + k] = seg[rank];
-        ++rank;
-      } else if (mode == 1) {
-        z[pix * K + k] = 0.0f;
-      }
+    s_m[c][threadIdx.x] = (uint16_t)m;
+    s_off[c][threadIdx.x] = (uint32_t)(seg_base[(int64_t)q * NC + c] - item_base) + (uint32_t)off;
+  }
+  __syncthreads();
+  const int npx = min(kStrip, it.W - it.js * kStrip);
+  float *zb = z + (it.base + (int64_t)it.a * it.W + it.js * kStrip) * K;
+  const int n = npx * K;
+  for (int j = threadIdx.x; j < n; j += kThreads) {
+    const int pl = j / K, k = j - pl * K;
+    const int c = k >> 4, e = k & 15;
+    const uint32_t m = s_m[c][pl];
+    if ((m >> e) & 1u) {
+      const uint64_t idx = item_base + s_off[c][pl] + __popc(m & ((1u << e) - 1u));
+      if (mode == 0) packed[idx] = zb[j];
+      else zb[j] = packed[idx];
+    } else if (mode == 1) {
+      zb[j] = 0.0f;
     }
   }
 }
