@@ -123,6 +123,24 @@ def peaks():
         return 6800.0, 1900.0, 1700.0, "fallback"
 
 
+def measured_traffic(kernel: str, npx: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu counters of the
+    small profiling workload, scaled by pixels; None if the kernel source has
+    changed since the counters were taken."""
+    import hashlib
+    names = {"adj_tc": "adj2_kernel", "synth_tc": "syn2_kernel"}
+    try:
+        with open(os.path.join(ROOT, "profiles", "tc_kernels_prof_workload_counters.json")) as f:
+            c = json.load(f)
+        with open(os.path.join(ROOT, c["source"]), "rb") as f:
+            if hashlib.sha1(f.read()).hexdigest() != c["source_sha1"]:
+                return None
+        k = c["kernels"][names[kernel]]
+        return k["dram_bytes_per_launch"] * npx / c["workload_pixels"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def launches_per_step(path: str, n_iters: int) -> int:
     """Kernels the library launches in one scsc_code_step (counted from the
     host orchestration): mask 1; power iteration 3 + 50 * 4 + 4; then
@@ -321,7 +339,8 @@ def main():
         if bytes_per_launch is not None:
             ach = bytes_per_launch / avg_s / 1e9
             roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": hbm, "unit": "GB/s",
-                    "frac": ach / hbm, "traffic": None, "peak_source": src,
+                    "frac": ach / hbm, "traffic": measured_traffic(dom, npx),
+                    "algorithmic_bytes": bytes_per_launch, "peak_source": src,
                     "avg_launch_ms": avg_s * 1e3}
 
     # end to end through the public API with host buffers
