@@ -58,14 +58,14 @@ struct SegIter {
 // Per-pixel chunk masks and exclusive offsets of the pixel's sampled values
 // inside the item's packed storage, from the staged mask words; one 128-thread
 // group (named barrier `bar`), thread e = pixel e, warp w of the group.
-__device__ __forceinline__ void chunk_offsets(const uint32_t *mw_s, int KW, int NC, int e, int w,
-                                              int lane, int *tot, int bar, uint32_t (&m)[kMaxNC],
+__device__ __forceinline__ void chunk_offsets(const uint32_t (&mw)[4], int NC, int w, int lane,
+                                              int *tot, int bar, uint32_t (&m)[kMaxNC],
                                               int (&off)[kMaxNC]) {
   int cnt[kMaxNC], incl[kMaxNC];
 #pragma unroll
   for (int c = 0; c < kMaxNC; ++c) {
     m[c] = 0u;
-    if (c < NC) m[c] = (mw_s[e * KW + (c >> 1)] >> ((c & 1) * 16)) & 0xFFFFu;
+    if (c < NC) m[c] = (mw[c >> 1] >> ((c & 1) * 16)) & 0xFFFFu;
     cnt[c] = __popc(m[c]);
     int x = cnt[c];
 #pragma unroll
@@ -95,22 +95,30 @@ __device__ __forceinline__ void chunk_offsets(const uint32_t *mw_s, int KW, int 
   }
 }
 
-// Issue cp.async copies of one item's packed codes [beg, end) (16-byte pieces)
-// and of its pixels' mask words into shared memory, as one commit group of
-// this thread.  `it` describes the item's strip; `a` is its row.
-__device__ __forceinline__ void prefetch_item(const Item &it, int a, uint64_t beg, uint64_t end,
-                                              int KW, const float *packed, const uint32_t *bits,
-                                              float *dv, uint32_t *dm, int e) {
-  const int nv4 = (int)((end - beg) >> 2);
-  for (int k = e; k < nv4; k += 128) tc::cp_async16(dv + 4 * k, packed + beg + 4 * (uint64_t)k);
-  const int b0 = it.js * kStrip;
-  const int npx = min(kStrip, it.W - b0);
-  const uint32_t *src = bits + (it.base + (int64_t)a * it.W + b0) * KW;
-  for (int k = e; k < kStrip * KW; k += 128) {
-    const bool in = k / KW < npx;
-    tc::cp_async4(dm + k, in ? src + k : bits, in ? 4u : 0u);
+// Mask words of pixel e of row a of the item's strip, into registers (zero
+// beyond the image).
+__device__ __forceinline__ void load_masks(const Item &it, int a, int KW, const uint32_t *bits,
+                                           int e, uint32_t (&mw)[4]) {
+  const int col = it.js * kStrip + e;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) mw[w] = 0u;
+  if (col < it.W) {
+    const uint32_t *src = bits + (it.base + (int64_t)a * it.W + col) * KW;
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+      if (w < KW) mw[w] = src[w];
   }
-  tc::cp_async_commit();
+}
+
+// One bulk copy of an item's packed codes [beg, end) (16-byte aligned, a
+// multiple of 4 floats) into shared memory; `bar` completes when it lands.
+// Issued by one thread, after a barrier that retired all earlier reads of dv.
+__device__ __forceinline__ void stage_item(uint64_t beg, uint64_t end, const float *packed,
+                                           float *dv, uint64_t *bar) {
+  const uint32_t bytes = (uint32_t)(end - beg) * 4u;
+  tc::fence_proxy_async();
+  tc::mbar_arrive_expect_tx(bar, bytes);
+  if (bytes) tc::bulk_g2s(dv, packed + beg, bytes, bar);
 }
 
 // Item following `it` (next row of the strip, or the first row of the next
@@ -136,7 +144,7 @@ struct Adj2 {
   __host__ __device__ static size_t vals_bytes(int Kp) { return (size_t)kStrip * Kp * 4; }
   __host__ __device__ static size_t mask_bytes(int KW) { return (size_t)kStrip * KW * 4; }
   __host__ __device__ static size_t total(int Kp, int KW) {
-    return 1024 + b_bytes(Kp) + (size_t)RS * kSRow + 2 * (vals_bytes(Kp) + mask_bytes(KW)) +
+    return 1024 + b_bytes(Kp) + (size_t)RS * kSRow + 2 * vals_bytes(Kp) +
            (size_t)kProd * 2 * 144 * 4 + 4 * kMaxNC * 4;
   }
 };
@@ -196,17 +204,12 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
   p += L::vals_bytes(Kp);
   float *const vals1 = reinterpret_cast<float *>(p);
   p += L::vals_bytes(Kp);
-  uint32_t *const msk0 = reinterpret_cast<uint32_t *>(p);
-  p += L::mask_bytes(KW);
-  uint32_t *const msk1 = reinterpret_cast<uint32_t *>(p);
-  p += L::mask_bytes(KW);
   auto vals = [&](int k) { return (k & 1) ? vals1 : vals0; };
-  auto msk = [&](int k) { return (k & 1) ? msk1 : msk0; };
   float *rst = reinterpret_cast<float *>(p);
   p += (size_t)L::kProd * 2 * 144 * 4;
   int *tot = reinterpret_cast<int *>(p);
 
-  __shared__ uint64_t ring_full[RS], ring_empty[RS], tfull[2], tempty[2], done_bar;
+  __shared__ uint64_t ring_full[RS], ring_empty[RS], tfull[2], tempty[2], stg_full[2], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
@@ -223,6 +226,7 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&tfull[i], 1);
       tc::mbar_init(&tempty[i], 4);
+      tc::mbar_init(&stg_full[i], 1);
     }
     tc::mbar_init(&done_bar, 1);
     abort_flag = 0;
@@ -357,29 +361,29 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
     // b0v..b2v = seg_base of items i, i + 1, i + 2 (b3v loaded a step early)
     Item cur = item_of(im, q_begin), nxt = cur;
     uint64_t b0v = 0, b1v = 0, b2v = 0;
+    uint32_t mw[4], mwn[4];
     if (n_items > 0) {
       b0v = seg_base[(int64_t)q_begin * NC];
       b1v = seg_base[(int64_t)(q_begin + 1) * NC];
-      prefetch_item(cur, cur.a, b0v, b1v, KW, packed, bits, vals(0), msk(0), e);
+      if (e == 0) stage_item(b0v, b1v, packed, vals(0), &stg_full[0]);
+      load_masks(cur, cur.a, KW, bits, e, mw);
       if (n_items > 1) nxt = next_item(im, cur);
       b2v = seg_base[(int64_t)min(q_begin + 2, Q) * NC];
     }
     for (int i = 0; i < n_items; ++i) {
       const int q = q_begin + i;
       const uint64_t b3v = seg_base[(int64_t)min(q + 3, Q) * NC];
-      if (i + 1 < n_items)
-        prefetch_item(nxt, nxt.a, b1v, b2v, KW, packed, bits, vals((i + 1) & 1),
-                      msk((i + 1) & 1), e);
-      else
-        tc::cp_async_commit();
-      tc::cp_async_wait<1>();
-      tc::named_sync(2, 128);
+      if (i + 1 < n_items) {
+        if (e == 0) stage_item(b1v, b2v, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
+        load_masks(nxt, nxt.a, KW, bits, e, mwn);
+      }
       uint32_t m[kMaxNC];
       int off[kMaxNC];
-      chunk_offsets(msk(i & 1), KW, NC, e, ew, lane, tot, 2, m, off);
+      chunk_offsets(mw, NC, ew, lane, tot, 2, m, off);
       const int b = i & 1;
-      bool okw = true;
-      if (e == 0)
+      bool okw = tc::mbar_wait_abortable(&stg_full[i & 1], (uint32_t)((i >> 1) & 1), abort_v,
+                                         kWaitNs);
+      if (e == 0 && okw)
         okw = tc::mbar_wait_abortable(&tfull[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
       if (tc::named_sync_or(2, 128, !okw)) break;
       tc::fence_after_sync();
@@ -405,8 +409,9 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
 #pragma unroll
         for (int e2 = 0; e2 < 16; ++e2) {
           const float gv = __uint_as_float(g[(c & 1) * 16 + e2]);
+          const float v = zv[e2] - alpha * gv;  // soft threshold as v - clamp(v, -thr, thr)
           tc::st_shared_if(dbase + 4u * __popc(m[c] & ((1u << e2) - 1u)),
-                           soft_threshold(zv[e2] - alpha * gv, thr), (m[c] >> e2) & 1u);
+                           v - fminf(fmaxf(v, -thr), thr), (m[c] >> e2) & 1u);
         }
       }
       tc::fence_before_sync();
@@ -418,12 +423,13 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
         *reinterpret_cast<float4 *>(packed + b0v + 4 * (uint64_t)k) =
             *reinterpret_cast<const float4 *>(dv + 4 * k);
       tc::named_sync(2, 128);  // the buffer is refilled by the prefetch two items on
+#pragma unroll
+      for (int w = 0; w < 4; ++w) mw[w] = mwn[w];
       b0v = b1v;
       b1v = b2v;
       b2v = b3v;
       if (i + 2 < n_items) nxt = next_item(im, nxt);
     }
-    tc::cp_async_wait<0>();
   }
 
   __syncthreads();
@@ -446,7 +452,7 @@ struct Syn2 {
   __host__ __device__ static size_t vals_bytes(int Kp) { return (size_t)kStrip * Kp * 4; }
   __host__ __device__ static size_t mask_bytes(int KW) { return (size_t)kStrip * KW * 4; }
   __host__ __device__ static size_t total(int Kp, int KW, int nst) {
-    return 1024 + a_bytes(Kp) + b_bytes(Kp) + (size_t)nst * (vals_bytes(Kp) + mask_bytes(KW)) +
+    return 1024 + a_bytes(Kp) + b_bytes(Kp) + (size_t)nst * vals_bytes(Kp) +
            (size_t)2 * 4 * 2 * S * S * 4 + 4 * kMaxNC * 4;
   }
 };
@@ -501,20 +507,12 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     vals1 = reinterpret_cast<float *>(p);
     p += L::vals_bytes(Kp);
   }
-  uint32_t *const msk0 = reinterpret_cast<uint32_t *>(p);
-  p += L::mask_bytes(KW);
-  uint32_t *msk1 = msk0;
-  if (nst == 2) {
-    msk1 = reinterpret_cast<uint32_t *>(p);
-    p += L::mask_bytes(KW);
-  }
   auto vals = [&](int k) { return (k & 1) ? vals1 : vals0; };
-  auto msk = [&](int k) { return (k & 1) ? msk1 : msk0; };
   float *Pu = reinterpret_cast<float *>(p);  // edge exchange of the col2im, [2][4][2c][S]
   p += (size_t)2 * 4 * 2 * S * S * 4;
   int *tot = reinterpret_cast<int *>(p);
 
-  __shared__ uint64_t tfull[2], tempty[2], a_free, done_bar;
+  __shared__ uint64_t tfull[2], tempty[2], stg_full[2], a_free, done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
@@ -527,6 +525,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&tfull[i], 1);
       tc::mbar_init(&tempty[i], 4);
+      tc::mbar_init(&stg_full[i], 1);
     }
     tc::mbar_init(&a_free, 1);
     tc::mbar_init(&done_bar, 1);
@@ -572,8 +571,13 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
       nb0 = base_of(nx.q());
       nb1 = base_of(nx.q() + 1);
     }
-    if (have && nst == 2)
-      prefetch_item(g.sg.it, g.a, gb0, gb1, KW, packed, bits, vals(0), msk(0), e);
+    // staged codes: one bulk copy per code row into vals(row parity) (or the
+    // single buffer); mask words: registers, loaded one row ahead
+    uint32_t mw[4], mwn[4];
+    if (have) {
+      if (e == 0) stage_item(gb0, gb1, packed, vals(0), &stg_full[0]);
+      load_masks(g.sg.it, g.a, KW, bits, e, mw);
+    }
     int i = 0;
     while (have) {
       CodeRowGen nn = nx;
@@ -584,23 +588,17 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
         mb1 = base_of(nn.q() + 1);
       }
       const int sb = nst == 2 ? (i & 1) : 0;
-      if (nst == 2) {
-        if (have_nx)
-          prefetch_item(nx.sg.it, nx.a, nb0, nb1, KW, packed, bits, vals((i + 1) & 1),
-                        msk((i + 1) & 1), e);
-        else
-          tc::cp_async_commit();
-        tc::cp_async_wait<1>();
-      } else {
-        prefetch_item(g.sg.it, g.a, gb0, gb1, KW, packed, bits, vals(0), msk(0), e);
-        tc::cp_async_wait<0>();
+      if (have_nx) {
+        if (nst == 2 && e == 0)
+          stage_item(nb0, nb1, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
+        load_masks(nx.sg.it, nx.a, KW, bits, e, mwn);
       }
-      tc::named_sync(1, 128);
       uint32_t m[kMaxNC];
       int off[kMaxNC];
-      chunk_offsets(msk(sb), KW, NC, e, ew, lane, tot, 1, m, off);
-      bool okw = true;
-      if (e == 0 && i > 0)
+      chunk_offsets(mw, NC, ew, lane, tot, 1, m, off);
+      const uint32_t use = (uint32_t)(nst == 2 ? (i >> 1) : i);
+      bool okw = tc::mbar_wait_abortable(&stg_full[sb], use & 1u, abort_v, kWaitNs);
+      if (e == 0 && i > 0 && okw)
         okw = tc::mbar_wait_abortable(&a_free, (uint32_t)((i - 1) & 1), abort_v, kWaitNs);
       if (tc::named_sync_or(1, 128, !okw)) break;
       const float *dv = vals(sb);
@@ -624,6 +622,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
       }
       tc::fence_proxy_async();
       tc::named_sync(1, 128);
+      if (nst == 1 && have_nx && e == 0) stage_item(nb0, nb1, packed, vals(0), &stg_full[0]);
       if (e == 0) {
         const int b = i & 1;
         bool okm = tc::mbar_wait_abortable(&tempty[b], (uint32_t)(((i >> 1) & 1) ^ 1), abort_v,
@@ -640,6 +639,8 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
           tc::mma_commit(&a_free);
         }
       }
+#pragma unroll
+      for (int w = 0; w < 4; ++w) mw[w] = mwn[w];
       g = nx;
       have = have_nx;
       gb0 = nb0;
@@ -650,7 +651,6 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
       nb1 = mb1;
       ++i;
     }
-    tc::cp_async_wait<0>();
     if (tid == 0) {
       tc::mma_commit(&done_bar);
       tc::mbar_wait_bounded(&done_bar, 0, kWaitNs);

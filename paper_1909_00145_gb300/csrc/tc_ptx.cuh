@@ -177,6 +177,25 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// ---- bulk copies (TMA engine, no tensor map) --------------------------------------
+
+// Arrive on `bar` and add `bytes` to the transaction count its phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Copy `bytes` (multiple of 16, both addresses 16-byte aligned) from global to
+// this CTA's shared memory; completion is counted on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // ---- predicated shared-memory access (no branches) -----------------------------
 
 __device__ __forceinline__ void st_shared_if(uint32_t saddr, float v, bool pred) {
@@ -185,6 +204,12 @@ __device__ __forceinline__ void st_shared_if(uint32_t saddr, float v, bool pred)
           saddr),
       "f"(v), "r"((uint32_t)pred)
       : "memory");
+}
+__device__ __forceinline__ void st_shared_u32(uint32_t saddr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(saddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_shared_f32(uint32_t saddr, float v) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(saddr), "f"(v) : "memory");
 }
 __device__ __forceinline__ float ld_shared(uint32_t saddr) {
   float v;
@@ -232,7 +257,7 @@ __device__ __forceinline__ bool mbar_wait_abortable(uint64_t *bar, uint32_t pari
       return false;
     }
     __nanosleep(ns);
-    if (ns < 256) ns <<= 1;
+    if (ns < 64) ns <<= 1;
   }
 }
 
