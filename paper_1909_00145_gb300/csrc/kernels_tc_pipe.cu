@@ -137,7 +137,8 @@ __device__ __forceinline__ Item next_item(const ItemMap &im, const Item &it) {
 template <int S>
 struct Adj2 {
   static constexpr int C = (S - 1) / 2;
-  static constexpr int RS = ((S + 3) + 1) & ~1;  // ring slots (even)
+  static constexpr int RS = 16;  // ring slots: a power of two >= S + 3 (slot = j & 15)
+  static_assert(S + 3 <= RS, "ring too small");
   static constexpr int kSRow = 17 * 128;
   static constexpr int kProd = 3;
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)S * Kp * 32; }
@@ -153,7 +154,7 @@ struct Adj2 {
 // them: per segment, rows o0 - c .. o1 - 1 + c; j counts them across segments.
 struct RowGen {
   SegIter sg;
-  int64_t j_seg, j;
+  int j_seg, j;  // 32-bit: a CTA's range holds far fewer than 2^31 rows
   int t, nrows;
   bool live;
   int C;
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
       const uint32_t idesc = tc::idesc_bf16_f32(128, Kp);
       const uint32_t ring_base = tc::smem_u32(ring), b_base = tc::smem_u32(Bs);
       SegIter sg{q_begin, q_end};
-      int64_t j_seg = 0;
+      int j_seg = 0;
       int i = 0;
       bool ok = true;
       while (ok && sg.next(im)) {
@@ -262,25 +263,25 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
           const int b = i & 1;
           const uint32_t use = (uint32_t)(i >> 1);
           ok = tc::mbar_wait_abortable(&tempty[b], (use & 1u) ^ 1u, abort_v, kWaitNs);
-          const int64_t jr = j_seg + (a - sg.o0);
+          const int jr = j_seg + (a - sg.o0);
           for (int u = 0; u < S && ok; ++u) {
-            const int64_t j = jr + u;
-            ok = tc::mbar_wait_abortable(&ring_full[j % RS], (uint32_t)((j / RS) & 1), abort_v,
+            const int j = jr + u;
+            ok = tc::mbar_wait_abortable(&ring_full[j & (RS - 1)], (uint32_t)((j / RS) & 1), abort_v,
                                          kWaitNs);
           }
           if (!ok) break;
           tc::fence_after_sync();
 #pragma unroll 1
           for (int u = 0; u < S; ++u) {
-            const uint32_t slot = (uint32_t)((jr + u) % RS);
+            const uint32_t slot = (uint32_t)((jr + u) & (RS - 1));
             uint64_t ad = tc::smem_desc(ring_base + slot * L::kSRow, 128, 128);
             uint64_t bd = tc::smem_desc(b_base + u * Kp * 32, Kp * 16, 128);
             tc::mma_bf16(taddr + b * 128, ad, bd, idesc, u > 0 ? 1u : 0u);
           }
           tc::mma_commit(&tfull[b]);
-          tc::mma_commit(&ring_empty[jr % RS]);
+          tc::mma_commit(&ring_empty[jr & (RS - 1)]);
           if (a == sg.o1 - 1)
-            for (int e2 = 1; e2 <= 2 * C; ++e2) tc::mma_commit(&ring_empty[(jr + e2) % RS]);
+            for (int e2 = 1; e2 <= 2 * C; ++e2) tc::mma_commit(&ring_empty[(jr + e2) & (RS - 1)]);
         }
         j_seg += nrows;
       }
@@ -319,8 +320,8 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
       bool have_next = next_mine(nxt);
       if (have_next) issue(nxt, sbuf ? stg0 : stg1);
       else tc::cp_async_commit();
-      const int64_t j = cur.j;
-      const int slot = (int)(j % RS);
+      const int j = cur.j;
+      const int slot = j & (RS - 1);
       bool w = true;
       if (lane == 0)
         w = tc::mbar_wait_abortable(&ring_empty[slot], (uint32_t)(((j / RS) & 1) ^ 1), abort_v,
