@@ -6,9 +6,11 @@
 // Items are ordered (n, js, a); a persistent CTA takes a contiguous range.
 //
 // Sampled codes (the pDK variables of Eq. 3) are stored packed in FP32,
-// chunk-major per item: for each 16-filter chunk c of item q, the sampled
-// values of its 128 pixels in pixel order, each pixel's in filter order,
-// starting at seg_base[q * NC + c].  Unsampled codes are not stored (Eq. 4).
+// pixel-major per item: the sampled values of pixel p of item q, in filter
+// order, start at seg_base[q] + pxoff[q * 128 + p].  Unsampled codes are not
+// stored (Eq. 4).  Each item is padded to a multiple of 4 floats (16-byte
+// aligned bulk copies).  seg_base and pxoff depend only on the mask M^t and
+// are built once per outer iteration.
 //
 // Synthesis  P[p][(u,v)] = sum_k z_k(a, b0+p) d_k(u,v)  (MMA, N = 16 s taps)
 //            xhat(a-c+u, b0+p-c+v) += P[p][(u,v)]       (col2im, registers)
@@ -66,23 +68,24 @@ __global__ void prep_filters_kernel(const float *d, int K, int S, int Kp, __nv_b
 
 // ------------------------------------------------------------------ packed layout
 
-__global__ void __launch_bounds__(kThreads) seg_count_kernel(ItemMap im, int KW, int NC,
+// Per item: its sampled-value count (padded to a multiple of 4) and the
+// exclusive offsets of its 128 pixels' values inside it.
+__global__ void __launch_bounds__(kThreads) seg_count_kernel(ItemMap im, int KW,
                                                              const uint32_t *bits,
-                                                             uint32_t *counts) {
+                                                             uint32_t *counts, uint16_t *pxoff) {
   __shared__ int sh[4];
   const int q = blockIdx.x;
   const Item it = item_of(im, q);
   const int col = it.js * kStrip + threadIdx.x;
-  int item_total = 0;
-  for (int c = 0; c < NC; ++c) {
-    int cnt = __popc(chunk_mask(bits, KW, it, it.a, col, c));
-    int total;
-    scan128(cnt, sh, total);
-    item_total += total;
-    // the last chunk carries the padding that keeps every item 16-byte aligned
-    if (c == NC - 1) total += (4 - (item_total & 3)) & 3;
-    if (threadIdx.x == 0) counts[(int64_t)q * NC + c] = (uint32_t)total;
+  int cnt = 0;
+  if (col < it.W) {
+    const uint32_t *w = bits + (it.base + (int64_t)it.a * it.W + col) * KW;
+    for (int k = 0; k < KW; ++k) cnt += __popc(w[k]);
   }
+  int total;
+  const int off = scan128(cnt, sh, total);
+  pxoff[(int64_t)q * kStrip + threadIdx.x] = (uint16_t)off;
+  if (threadIdx.x == 0) counts[q] = (uint32_t)(total + ((4 - (total & 3)) & 3));
 }
 
 // Exclusive scan u32 -> u64 in three passes over blocks of 1024 elements.
@@ -136,21 +139,21 @@ __global__ void scan_add_kernel(uint64_t *out, int n, const uint64_t *block_sums
 constexpr int kMaxChunks = 16;  // K <= 256
 __global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int KW, int NC,
                                                         const uint32_t *bits,
-                                                        const uint64_t *seg_base, float *packed,
+                                                        const uint64_t *seg_base,
+                                                        const uint16_t *pxoff, float *packed,
                                                         float *z, int mode) {
-  __shared__ int sh[4];
   __shared__ uint16_t s_m[kMaxChunks][kStrip];
   __shared__ uint32_t s_off[kMaxChunks][kStrip];
   const int q = blockIdx.x;
   const Item it = item_of(im, q);
   const int col = it.js * kStrip + threadIdx.x;
-  const uint64_t item_base = seg_base[(int64_t)q * NC];
+  const uint64_t item_base = seg_base[q];
+  uint32_t run = pxoff[(int64_t)q * kStrip + threadIdx.x];
   for (int c = 0; c < NC; ++c) {
-    uint32_t m = chunk_mask(bits, KW, it, it.a, col, c);
-    int total;
-    int off = scan128(__popc(m), sh, total);
+    const uint32_t m = chunk_mask(bits, KW, it, it.a, col, c);
     s_m[c][threadIdx.x] = (uint16_t)m;
-    s_off[c][threadIdx.x] = (uint32_t)(seg_base[(int64_t)q * NC + c] - item_base) + (uint32_t)off;
+    s_off[c][threadIdx.x] = run;
+    run += __popc(m);
   }
   __syncthreads();
   const int npx = min(kStrip, it.W - it.js * kStrip);
@@ -179,8 +182,7 @@ struct SynthSmem {
   __host__ __device__ static size_t a_bytes(int Kp) { return (size_t)kStrip * Kp * 2; }
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)N * Kp * 2; }
   __host__ __device__ static size_t total(int Kp) {
-    return 1024 + a_bytes(Kp) + b_bytes(Kp) + (size_t)kStrip * 16 * 4 +
-           (size_t)2 * S * kPuRow * 4;
+    return 1024 + a_bytes(Kp) + b_bytes(Kp) + (size_t)2 * S * kPuRow * 4;
   }
 };
 
@@ -188,6 +190,7 @@ template <int S>
 __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, int Kp, int KW,
                                                             const uint32_t *__restrict__ bits,
                                                             const uint64_t *__restrict__ seg_base,
+                                                            const uint16_t *__restrict__ pxoff,
                                                             const float *__restrict__ packed,
                                                             const uint4 *__restrict__ bsyn,
                                                             float *__restrict__ xcore,
@@ -199,11 +202,9 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
   uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *As = smem;
   uint8_t *Bs = As + L::a_bytes(Kp);
-  float *stage = reinterpret_cast<float *>(Bs + L::b_bytes(Kp));
-  float *Pu = stage + kStrip * 16;  // [2][S][kPuRow]
+  float *Pu = reinterpret_cast<float *>(Bs + L::b_bytes(Kp));  // [2][S][kPuRow]
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  __shared__ int sh[4];
 
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
@@ -250,20 +251,16 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
 
     for (int a = a_start; a < a_end; ++a) {
       const int qa = it.q_row0 + a;
-      // 1. expand the packed codes of code row a into the A operand (BF16)
+      // 1. expand the packed codes of code row a (this thread: pixel i) into
+      // the A operand (BF16)
+      const float *src = packed + seg_base[qa] + pxoff[(int64_t)qa * kStrip + i];
       for (int c = 0; c < NC; ++c) {
-        uint32_t m = chunk_mask(bits, KW, it, a, b0 + i, c);
-        int total;
-        int off = scan128(__popc(m), sh, total);
-        const float *src = packed + seg_base[(int64_t)qa * NC + c];
-        for (int j = tid; j < total; j += kThreads) stage[j] = src[j];
-        __syncthreads();
+        const uint32_t m = chunk_mask(bits, KW, it, a, b0 + i, c);
         float v[16];
-        int rank = 0;
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          v[e] = ((m >> e) & 1u) ? stage[off + rank] : 0.0f;
-          rank += (m >> e) & 1u;
+          v[e] = ((m >> e) & 1u) ? __ldg(src) : 0.0f;
+          src += (m >> e) & 1u;
         }
         uint4 lo = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
                               pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
@@ -272,7 +269,6 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
         uint8_t *dst = As + (size_t)(2 * c) * 2048 + (i >> 3) * 128 + (i & 7) * 16;
         *reinterpret_cast<uint4 *>(dst) = lo;
         *reinterpret_cast<uint4 *>(dst + 2048) = hi;
-        __syncthreads();
       }
       tc::fence_proxy_async();
       __syncthreads();
@@ -382,7 +378,7 @@ struct AdjSmem {
   static constexpr int kSRow = 17 * 128;  // one Toeplitz residual row (17 blocks)
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)S * Kp * 32; }
   __host__ __device__ static size_t total(int Kp) {
-    return 1024 + b_bytes(Kp) + (size_t)S * kSRow + 144 * 4 + (size_t)kStrip * 16 * 4;
+    return 1024 + b_bytes(Kp) + (size_t)S * kSRow + 144 * 4;
   }
 };
 
@@ -396,6 +392,7 @@ template <int S>
 __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int Kp, int KW,
                                                           const uint32_t *__restrict__ bits,
                                                           const uint64_t *__restrict__ seg_base,
+                                                          const uint16_t *__restrict__ pxoff,
                                                           float *__restrict__ packed,
                                                           const uint4 *__restrict__ badj,
                                                           const float *__restrict__ r,
@@ -410,10 +407,8 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
   uint8_t *Bs = smem;
   uint8_t *ring = Bs + L::b_bytes(Kp);
   float *rstage = reinterpret_cast<float *>(ring + (size_t)S * L::kSRow);
-  float *stage = rstage + 144;
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  __shared__ int sh[4];
 
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
@@ -498,27 +493,19 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
         break;
       }
       tc::fence_after_sync();
-      // prox on the packed sampled codes of this item, chunk by chunk
+      // prox on the packed sampled codes of this item (this thread: pixel i)
+      float *dst = packed + seg_base[qa] + pxoff[(int64_t)qa * kStrip + i];
       for (int c = 0; c < NC; ++c) {
-        uint32_t m = chunk_mask(bits, KW, it0, a, b0 + i, c);
-        int total;
-        int off = scan128(__popc(m), sh, total);
-        float *seg = packed + seg_base[(int64_t)qa * NC + c];
-        for (int j = tid; j < total; j += kThreads) stage[j] = seg[j];
+        const uint32_t m = chunk_mask(bits, KW, it0, a, b0 + i, c);
         float g[16];
         tc::tmem_ld16(lane_addr + 16 * c, g);
-        __syncthreads();
-        int rank = off;
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           if ((m >> e) & 1u) {
-            stage[rank] = soft_threshold(stage[rank] - alpha * g[e], thr);
-            ++rank;
+            *dst = soft_threshold(*dst - alpha * g[e], thr);
+            ++dst;
           }
         }
-        __syncthreads();
-        for (int j = tid; j < total; j += kThreads) seg[j] = stage[j];
-        __syncthreads();
       }
       tc::fence_before_sync();
       __syncthreads();
@@ -642,12 +629,13 @@ T *as(const TcWorkspace::Buf &b) {
 }  // namespace
 
 cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
-                        const uint64_t *seg_base, const float *packed, const uint4 *bsyn,
-                        float *xcore, float *spill, int *err, int grid, int max_smem,
-                        cudaStream_t st);
+                        const uint64_t *seg_base, const uint16_t *pxoff, const float *packed,
+                        const uint4 *bsyn, float *xcore, float *spill, int *err, int grid,
+                        int max_smem, cudaStream_t st);
 cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
-                        const uint64_t *seg_base, float *packed, const uint4 *badj, const float *r,
-                        const StepParams *prm, int *err, int grid, cudaStream_t st);
+                        const uint64_t *seg_base, const uint16_t *pxoff, float *packed,
+                        const uint4 *badj, const float *r, const StepParams *prm, int *err,
+                        int grid, cudaStream_t st);
 cudaError_t prepare_pipe(int K, int s, int max_smem);
 
 int *tc_error_word(TcWorkspace &ws) {
@@ -660,8 +648,9 @@ const char *tc_last_error(const TcWorkspace &ws) { return ws.last_error.c_str();
 void tc_release(TcWorkspace &ws) {
   if (ws.graph_exec) cudaGraphExecDestroy(ws.graph_exec);
   ws.graph_exec = nullptr;
-  for (TcWorkspace::Buf *b : {&ws.item0, &ws.seg_count, &ws.seg_base, &ws.scan_blocks, &ws.packed,
-                              &ws.xcore, &ws.spill, &ws.r, &ws.badj, &ws.bsyn, &ws.err}) {
+  for (TcWorkspace::Buf *b : {&ws.item0, &ws.seg_count, &ws.seg_base, &ws.pxoff, &ws.scan_blocks,
+                              &ws.packed, &ws.xcore, &ws.spill, &ws.r, &ws.badj, &ws.bsyn,
+                              &ws.err}) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
     b->bytes = 0;
@@ -707,10 +696,11 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   }
   const int Q = ws.n_items;
   ItemMap im{n, as<int>(ws.item0), b.H, b.W, b.off, Q};
-  const int64_t nseg = (int64_t)Q * NC;
+  const int64_t nseg = Q;
   const int nblk = (int)((nseg + 1023) / 1024);
   TRY(ensure(ws.seg_count, (size_t)nseg * 4));
   TRY(ensure(ws.seg_base, (size_t)(nseg + 1) * 8));
+  TRY(ensure(ws.pxoff, (size_t)nseg * kStrip * 2));
   TRY(ensure(ws.scan_blocks, (size_t)(nblk + 1) * 8));
   TRY(ensure(ws.packed, ((size_t)b.total_px * K + 4 * (size_t)Q + 16) * 4));
   TRY(ensure(ws.xcore, (size_t)b.total_px * 4));
@@ -725,7 +715,8 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
                                           as<__nv_bfloat16>(ws.bsyn));
   TRY(cudaGetLastError());
   if (Q == 0) return cudaSuccess;
-  seg_count_kernel<<<Q, kThreads, 0, st>>>(im, KW, NC, bits, as<uint32_t>(ws.seg_count));
+  uint16_t *pxoff = as<uint16_t>(ws.pxoff);
+  seg_count_kernel<<<Q, kThreads, 0, st>>>(im, KW, bits, as<uint32_t>(ws.seg_count), pxoff);
   TRY(cudaGetLastError());
   uint64_t *seg_base = as<uint64_t>(ws.seg_base);
   scan_local_kernel<<<nblk, 1024, 0, st>>>(as<uint32_t>(ws.seg_count), seg_base, (int)nseg,
@@ -736,7 +727,8 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   scan_add_kernel<<<nblk, 1024, 0, st>>>(seg_base, (int)nseg, as<uint64_t>(ws.scan_blocks));
   TRY(cudaGetLastError());
   int pr = ws.prof ? ws.prof->begin(KID_PACK, st) : -1;
-  pack_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, as<float>(ws.packed), z, 0);
+  pack_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, pxoff, as<float>(ws.packed),
+                                      z, 0);
   TRY(cudaGetLastError());
   if (ws.prof) ws.prof->end(pr, st);
 
@@ -777,14 +769,14 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   auto iteration = [&](int v) -> cudaError_t {
     int p1 = ws.prof ? ws.prof->begin(KID_SYNTH_TC, st) : -1;
     if (v == 1) {
-      TRY(launch_syn2(im, K, s, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.bsyn),
+      TRY(launch_syn2(im, K, s, bits, seg_base, pxoff, as<float>(ws.packed), as<uint4>(ws.bsyn),
                       as<float>(ws.xcore), as<float>(ws.spill), as<int>(ws.err), grid2,
                       ws.max_smem, st));
     } else {
       TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
         constexpr int S = decltype(SC)::value;
         synth_tc_kernel<S><<<grid_s1, kThreads, smem_s1, st>>>(
-            im, K, Kp, KW, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.bsyn),
+            im, K, Kp, KW, bits, seg_base, pxoff, as<float>(ws.packed), as<uint4>(ws.bsyn),
             as<float>(ws.xcore), as<float>(ws.spill), as<int>(ws.err));
         return cudaGetLastError();
       }));
@@ -797,13 +789,13 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
     if (ws.prof) ws.prof->end(p2, st);
     int p3 = ws.prof ? ws.prof->begin(KID_ADJ_TC, st) : -1;
     if (v == 1) {
-      TRY(launch_adj2(im, K, s, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.badj),
+      TRY(launch_adj2(im, K, s, bits, seg_base, pxoff, as<float>(ws.packed), as<uint4>(ws.badj),
                       as<float>(ws.r), prm, as<int>(ws.err), grid2, st));
     } else {
       TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
         constexpr int S = decltype(SC)::value;
         adj_tc_kernel<S><<<grid_a1, kThreads, smem_a1, st>>>(
-            im, K, Kp, KW, bits, seg_base, as<float>(ws.packed), as<uint4>(ws.badj),
+            im, K, Kp, KW, bits, seg_base, pxoff, as<float>(ws.packed), as<uint4>(ws.badj),
             as<float>(ws.r), prm, as<int>(ws.err));
         return cudaGetLastError();
       }));
@@ -858,8 +850,9 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   const bool use_graph = ws.graphs && rem > 0 && st != nullptr && !user_capture &&
                          !(ws.prof && ws.prof->on);
   if (use_graph) {
-    const GraphKey gk{bits, seg_base, ws.packed.p, ws.bsyn.p, ws.badj.p, ws.xcore.p, ws.spill.p,
-                      ws.r.p, ws.err.p, x, prm, ws.item0.p, b.off, K, s, Q, variant, rem};
+    const GraphKey gk{bits, seg_base, pxoff, ws.packed.p, ws.bsyn.p, ws.badj.p, ws.xcore.p,
+                      ws.spill.p, ws.r.p, ws.err.p, x, prm, ws.item0.p, b.off, K, s, Q,
+                      variant, rem};
     if (!ws.graph_exec || std::memcmp(&gk, &ws.graph_key, sizeof gk) != 0) {
       if (ws.graph_exec) cudaGraphExecDestroy(ws.graph_exec);
       ws.graph_exec = nullptr;
@@ -880,7 +873,8 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   }
   // Eq. 4: dense codes, zero off the sampled set
   int pu = ws.prof ? ws.prof->begin(KID_UNPACK, st) : -1;
-  pack_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, as<float>(ws.packed), z, 1);
+  pack_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, pxoff, as<float>(ws.packed),
+                                      z, 1);
   TRY(cudaGetLastError());
   if (ws.prof) ws.prof->end(pu, st);
   return cudaSuccess;

@@ -27,8 +27,6 @@ namespace {
 using namespace tcitems;
 
 constexpr uint64_t kWaitNs = 1000000000ull;
-constexpr int kPad = 10;
-constexpr int kPuRow = kStrip + 2 * kPad;
 constexpr int kMaxNC = 8;  // Kp <= 128
 
 // Offset the dynamic shared-memory base to a 1024-byte boundary by pointer
@@ -55,50 +53,11 @@ struct SegIter {
   }
 };
 
-// Per-pixel chunk masks and exclusive offsets of the pixel's sampled values
-// inside the item's packed storage, from the staged mask words; one 128-thread
-// group (named barrier `bar`), thread e = pixel e, warp w of the group.
-__device__ __forceinline__ void chunk_offsets(const uint32_t (&mw)[4], int NC, int w, int lane,
-                                              int *tot, int bar, uint32_t (&m)[kMaxNC],
-                                              int (&off)[kMaxNC]) {
-  int cnt[kMaxNC], incl[kMaxNC];
-#pragma unroll
-  for (int c = 0; c < kMaxNC; ++c) {
-    m[c] = 0u;
-    if (c < NC) m[c] = (mw[c >> 1] >> ((c & 1) * 16)) & 0xFFFFu;
-    cnt[c] = __popc(m[c]);
-    int x = cnt[c];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    incl[c] = x;
-  }
-  if (lane == 31) {
-#pragma unroll
-    for (int c = 0; c < kMaxNC; ++c) tot[w * kMaxNC + c] = incl[c];
-  }
-  tc::named_sync(bar, 128);
-  int base = 0;
-#pragma unroll
-  for (int c = 0; c < kMaxNC; ++c) {
-    int pre = 0, ct = 0;
-#pragma unroll
-    for (int w2 = 0; w2 < 4; ++w2) {
-      int v = tot[w2 * kMaxNC + c];
-      pre += (w2 < w) ? v : 0;
-      ct += v;
-    }
-    off[c] = base + pre + incl[c] - cnt[c];
-    base += ct;
-  }
-}
-
-// Mask words of pixel e of row a of the item's strip, into registers (zero
-// beyond the image).
+// Mask words of pixel e of row a of the item's strip (zero beyond the image)
+// and the offset of the pixel's sampled values inside the item, into registers.
 __device__ __forceinline__ void load_masks(const Item &it, int a, int KW, const uint32_t *bits,
-                                           int e, uint32_t (&mw)[4]) {
+                                           const uint16_t *pxoff, int e, uint32_t (&mw)[4],
+                                           uint32_t &po) {
   const int col = it.js * kStrip + e;
 #pragma unroll
   for (int w = 0; w < 4; ++w) mw[w] = 0u;
@@ -108,6 +67,12 @@ __device__ __forceinline__ void load_masks(const Item &it, int a, int KW, const 
     for (int w = 0; w < 4; ++w)
       if (w < KW) mw[w] = src[w];
   }
+  po = pxoff[(int64_t)(it.q_row0 + a) * kStrip + e];
+}
+
+// 16-bit sampled mask of filter chunk c from a pixel's mask words.
+__device__ __forceinline__ uint32_t chunk_bits(const uint32_t (&mw)[4], int c) {
+  return (mw[c >> 1] >> ((c & 1) * 16)) & 0xFFFFu;
 }
 
 // One bulk copy of an item's packed codes [beg, end) (16-byte aligned, a
@@ -141,12 +106,16 @@ struct Adj2 {
   static_assert(S + 3 <= RS, "ring too small");
   static constexpr int kSRow = 17 * 128;
   static constexpr int kProd = 3;
+  // Epilogue: kEpi groups of four warps; each covers all 128 pixels (TMEM lane
+  // quarters) and a share of the filter chunks.
+  static constexpr int kEpi = 2;
+  static constexpr int kThreads = 32 * (1 + kProd + 4 * kEpi);
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)S * Kp * 32; }
   __host__ __device__ static size_t vals_bytes(int Kp) { return (size_t)kStrip * Kp * 4; }
   __host__ __device__ static size_t mask_bytes(int KW) { return (size_t)kStrip * KW * 4; }
   __host__ __device__ static size_t total(int Kp, int KW) {
     return 1024 + b_bytes(Kp) + (size_t)RS * kSRow + 2 * vals_bytes(Kp) +
-           (size_t)kProd * 2 * 144 * 4 + 4 * kMaxNC * 4;
+           (size_t)kProd * 2 * 144 * 4;
   }
 };
 
@@ -185,9 +154,10 @@ struct RowGen {
 };
 
 template <int S>
-__global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp, int KW,
+__global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, int K, int Kp, int KW,
                                                       const uint32_t *__restrict__ bits,
                                                       const uint64_t *__restrict__ seg_base,
+                                                      const uint16_t *__restrict__ pxoff,
                                                       float *__restrict__ packed,
                                                       const uint4 *__restrict__ badj,
                                                       const float *__restrict__ r,
@@ -207,8 +177,6 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
   p += L::vals_bytes(Kp);
   auto vals = [&](int k) { return (k & 1) ? vals1 : vals0; };
   float *rst = reinterpret_cast<float *>(p);
-  p += (size_t)L::kProd * 2 * 144 * 4;
-  int *tot = reinterpret_cast<int *>(p);
 
   __shared__ uint64_t ring_full[RS], ring_empty[RS], tfull[2], tempty[2], stg_full[2], done_bar;
   __shared__ uint32_t tmem_base;
@@ -226,7 +194,7 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
     }
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&tfull[i], 1);
-      tc::mbar_init(&tempty[i], 4);
+      tc::mbar_init(&tempty[i], 4 * L::kEpi);
       tc::mbar_init(&stg_full[i], 1);
     }
     tc::mbar_init(&done_bar, 1);
@@ -264,7 +232,9 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
           const uint32_t use = (uint32_t)(i >> 1);
           ok = tc::mbar_wait_abortable(&tempty[b], (use & 1u) ^ 1u, abort_v, kWaitNs);
           const int jr = j_seg + (a - sg.o0);
-          for (int u = 0; u < S && ok; ++u) {
+          // rows jr .. jr + S - 2 were waited for by the previous row of the
+          // segment; only the first row of a segment waits for its whole window
+          for (int u = (a == sg.o0 ? 0 : S - 1); u < S && ok; ++u) {
             const int j = jr + u;
             ok = tc::mbar_wait_abortable(&ring_full[j & (RS - 1)], (uint32_t)((j / RS) & 1), abort_v,
                                          kWaitNs);
@@ -352,80 +322,94 @@ __global__ void __launch_bounds__(256, 1) adj2_kernel(ItemMap im, int K, int Kp,
     tc::cp_async_wait<0>();
   } else {
     // ------------------------------------------------ epilogue: prox on packed codes
-    const int e = tid - 128, ew = e >> 5;
+    // thread e: pixel px = e & 127 (TMEM lane), group gi = chunks [c_lo, c_hi)
+    constexpr int kE = 128 * L::kEpi;  // epilogue threads (named barrier 1)
+    const int e = tid - 128, px = e & 127, gi = e >> 7, ew = px >> 5;
+    const int npair = (NC + 1) / 2;  // chunk pairs share a TMEM load; groups split the pairs
+    const int c_lo = 2 * (gi * npair / L::kEpi);
+    const int c_hi = min(NC, 2 * ((gi + 1) * npair / L::kEpi));
     const float alpha = prm->alpha, thr = prm->thresh;
     const int n_items = q_end - q_begin;
-    const int Qv = Q;
-    (void)Qv;
     const uint32_t lane_base = taddr + ((uint32_t)(32 * ew) << 16);
     // item bookkeeping one step ahead: cur = item i, nxt = item i + 1;
     // b0v..b2v = seg_base of items i, i + 1, i + 2 (b3v loaded a step early)
     Item cur = item_of(im, q_begin), nxt = cur;
     uint64_t b0v = 0, b1v = 0, b2v = 0;
-    uint32_t mw[4], mwn[4];
+    uint32_t mw[4], mwn[4], po = 0, pon = 0;
     if (n_items > 0) {
-      b0v = seg_base[(int64_t)q_begin * NC];
-      b1v = seg_base[(int64_t)(q_begin + 1) * NC];
+      b0v = seg_base[q_begin];
+      b1v = seg_base[q_begin + 1];
       if (e == 0) stage_item(b0v, b1v, packed, vals(0), &stg_full[0]);
-      load_masks(cur, cur.a, KW, bits, e, mw);
+      load_masks(cur, cur.a, KW, bits, pxoff, px, mw, po);
       if (n_items > 1) nxt = next_item(im, cur);
-      b2v = seg_base[(int64_t)min(q_begin + 2, Q) * NC];
+      b2v = seg_base[min(q_begin + 2, Q)];
     }
     for (int i = 0; i < n_items; ++i) {
       const int q = q_begin + i;
-      const uint64_t b3v = seg_base[(int64_t)min(q + 3, Q) * NC];
+      const uint64_t b3v = seg_base[min(q + 3, Q)];
       if (i + 1 < n_items) {
         if (e == 0) stage_item(b1v, b2v, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
-        load_masks(nxt, nxt.a, KW, bits, e, mwn);
+        load_masks(nxt, nxt.a, KW, bits, pxoff, px, mwn, pon);
       }
-      uint32_t m[kMaxNC];
-      int off[kMaxNC];
-      chunk_offsets(mw, NC, ew, lane, tot, 2, m, off);
+      // this pixel's first value of chunk c_lo inside the staged item
+      uint32_t first = po;
+#pragma unroll
+      for (int c = 0; c < kMaxNC; ++c)
+        if (c < c_lo) first += __popc(chunk_bits(mw, c));
       const int b = i & 1;
       bool okw = tc::mbar_wait_abortable(&stg_full[i & 1], (uint32_t)((i >> 1) & 1), abort_v,
                                          kWaitNs);
       if (e == 0 && okw)
         okw = tc::mbar_wait_abortable(&tfull[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
-      if (tc::named_sync_or(2, 128, !okw)) break;
+      if (tc::named_sync_or(1, kE, !okw)) break;
       tc::fence_after_sync();
       float *dv = vals(i & 1);
       uint32_t g[32];  // accumulator columns of two chunks (32 filters)
+      // running address of the pixel's next sampled value (filter order)
+      uint32_t a_run = tc::smem_u32(dv) + 4u * first;
 #pragma unroll
       for (int c = 0; c < kMaxNC; ++c) {
-        if (c >= NC) break;
-        if ((c & 1) == 0) {
+        if (c < c_lo) continue;
+        if (c >= c_hi) break;
+        const uint32_t mc = chunk_bits(mw, c);
+        if (((c - c_lo) & 1) == 0) {  // c_lo is even: pairs (c, c + 1) share one load
           __syncwarp();
           tc::tmem_ld32_nowait(lane_base + b * 128 + 16 * c, g);
           tc::tmem_ld_wait();
         }
-        // slot of filter e2 = chunk offset + number of sampled filters below e2:
-        // all loads are independent, then all stores
-        // Loads are unconditional (an unsampled slot's index still lies inside
-        // the staged item) and stores predicated, so the loop has no branches.
-        const uint32_t dbase = tc::smem_u32(dv) + 4u * (uint32_t)off[c];
+        // slot of filter e2 = the running address: all loads are independent,
+        // then all stores.  Loads are unconditional (an unsampled filter's
+        // address still lies inside the staged item) and stores predicated,
+        // so the loop has no branches.
         float zv[16];
+        uint32_t ad[16];
+#pragma unroll
+        for (int e2 = 0; e2 < 16; ++e2) {
+          ad[e2] = a_run;
+          a_run += ((mc >> e2) & 1u) << 2;
+        }
 #pragma unroll
         for (int e2 = 0; e2 < 16; ++e2)
-          zv[e2] = tc::ld_shared(dbase + 4u * __popc(m[c] & ((1u << e2) - 1u)));
+          zv[e2] = tc::ld_shared(ad[e2]);
 #pragma unroll
         for (int e2 = 0; e2 < 16; ++e2) {
           const float gv = __uint_as_float(g[(c & 1) * 16 + e2]);
           const float v = zv[e2] - alpha * gv;  // soft threshold as v - clamp(v, -thr, thr)
-          tc::st_shared_if(dbase + 4u * __popc(m[c] & ((1u << e2) - 1u)),
-                           v - fminf(fmaxf(v, -thr), thr), (m[c] >> e2) & 1u);
+          tc::st_shared_if(ad[e2], v - fminf(fmaxf(v, -thr), thr), (mc >> e2) & 1u);
         }
       }
       tc::fence_before_sync();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
-      tc::named_sync(2, 128);
+      tc::named_sync(1, kE);
       const int nv4 = (int)((b1v - b0v) >> 2);
-      for (int k = e; k < nv4; k += 128)
+      for (int k = e; k < nv4; k += kE)
         *reinterpret_cast<float4 *>(packed + b0v + 4 * (uint64_t)k) =
             *reinterpret_cast<const float4 *>(dv + 4 * k);
-      tc::named_sync(2, 128);  // the buffer is refilled by the prefetch two items on
+      tc::named_sync(1, kE);  // the buffer is refilled by the prefetch two items on
 #pragma unroll
       for (int w = 0; w < 4; ++w) mw[w] = mwn[w];
+      po = pon;
       b0v = b1v;
       b1v = b2v;
       b2v = b3v;
@@ -454,7 +438,7 @@ struct Syn2 {
   __host__ __device__ static size_t mask_bytes(int KW) { return (size_t)kStrip * KW * 4; }
   __host__ __device__ static size_t total(int Kp, int KW, int nst) {
     return 1024 + a_bytes(Kp) + b_bytes(Kp) + (size_t)nst * vals_bytes(Kp) +
-           (size_t)2 * 4 * 2 * S * S * 4 + 4 * kMaxNC * 4;
+           (size_t)2 * 4 * 2 * S * S * 4;
   }
 };
 
@@ -489,6 +473,7 @@ template <int S>
 __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp, int KW, int nst,
                                                       const uint32_t *__restrict__ bits,
                                                       const uint64_t *__restrict__ seg_base,
+                                                      const uint16_t *__restrict__ pxoff,
                                                       const float *__restrict__ packed,
                                                       const uint4 *__restrict__ bsyn,
                                                       float *__restrict__ xcore,
@@ -510,8 +495,6 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
   }
   auto vals = [&](int k) { return (k & 1) ? vals1 : vals0; };
   float *Pu = reinterpret_cast<float *>(p);  // edge exchange of the col2im, [2][4][2c][S]
-  p += (size_t)2 * 4 * 2 * S * S * 4;
-  int *tot = reinterpret_cast<int *>(p);
 
   __shared__ uint64_t tfull[2], tempty[2], stg_full[2], a_free, done_bar;
   __shared__ uint32_t tmem_base;
@@ -551,13 +534,13 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
 
   if (warp < 4) {
     // ------------------------------------------------ producers + MMA issue
-    const int e = tid, ew = warp;
+    const int e = tid;
     const uint32_t idesc = tc::idesc_bf16_f32(128, N);
     const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
     const uint32_t b_lbo = 2 * S * 128;
     // code rows in sequence: g (current), nx (next), nn (after next); the
     // seg_base values of each row are loaded one iteration before they are used
-    auto base_of = [&](int qq) { return seg_base[(int64_t)qq * NC]; };
+    auto base_of = [&](int qq) { return seg_base[qq]; };
     CodeRowGen g;
     g.init(q_begin, q_end, C);
     bool have = g.next(im);
@@ -574,10 +557,10 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     }
     // staged codes: one bulk copy per code row into vals(row parity) (or the
     // single buffer); mask words: registers, loaded one row ahead
-    uint32_t mw[4], mwn[4];
+    uint32_t mw[4], mwn[4], po = 0, pon = 0;
     if (have) {
       if (e == 0) stage_item(gb0, gb1, packed, vals(0), &stg_full[0]);
-      load_masks(g.sg.it, g.a, KW, bits, e, mw);
+      load_masks(g.sg.it, g.a, KW, bits, pxoff, e, mw, po);
     }
     int i = 0;
     while (have) {
@@ -592,26 +575,26 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
       if (have_nx) {
         if (nst == 2 && e == 0)
           stage_item(nb0, nb1, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
-        load_masks(nx.sg.it, nx.a, KW, bits, e, mwn);
+        load_masks(nx.sg.it, nx.a, KW, bits, pxoff, e, mwn, pon);
       }
-      uint32_t m[kMaxNC];
-      int off[kMaxNC];
-      chunk_offsets(mw, NC, ew, lane, tot, 1, m, off);
       const uint32_t use = (uint32_t)(nst == 2 ? (i >> 1) : i);
       bool okw = tc::mbar_wait_abortable(&stg_full[sb], use & 1u, abort_v, kWaitNs);
       if (e == 0 && i > 0 && okw)
         okw = tc::mbar_wait_abortable(&a_free, (uint32_t)((i - 1) & 1), abort_v, kWaitNs);
       if (tc::named_sync_or(1, 128, !okw)) break;
       const float *dv = vals(sb);
+      // running address of the pixel's next sampled value (filter order)
+      uint32_t a_run = tc::smem_u32(dv) + 4u * po;
 #pragma unroll
       for (int c = 0; c < kMaxNC; ++c) {
         if (c >= NC) break;
+        const uint32_t mc = chunk_bits(mw, c);
         float v[16];
-        const uint32_t dbase = tc::smem_u32(dv) + 4u * (uint32_t)off[c];
 #pragma unroll
         for (int e2 = 0; e2 < 16; ++e2) {
-          const float t = tc::ld_shared(dbase + 4u * __popc(m[c] & ((1u << e2) - 1u)));
-          v[e2] = ((m[c] >> e2) & 1u) ? t : 0.0f;
+          const float t = tc::ld_shared(a_run);
+          v[e2] = ((mc >> e2) & 1u) ? t : 0.0f;
+          a_run += ((mc >> e2) & 1u) << 2;
         }
         uint4 lo = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
                               pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
@@ -642,6 +625,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
       }
 #pragma unroll
       for (int w = 0; w < 4; ++w) mw[w] = mwn[w];
+      po = pon;
       g = nx;
       have = have_nx;
       gb0 = nb0;
@@ -822,29 +806,30 @@ cudaError_t prepare_pipe(int K, int s, int max_smem) {
 }
 
 cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
-                        const uint64_t *seg_base, const float *packed, const uint4 *bsyn,
-                        float *xcore, float *spill, int *err, int grid, int max_smem,
-                        cudaStream_t st) {
+                        const uint64_t *seg_base, const uint16_t *pxoff, const float *packed,
+                        const uint4 *bsyn, float *xcore, float *spill, int *err, int grid,
+                        int max_smem, cudaStream_t st) {
   const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
   return dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
     int nst = Syn2<S>::total(Kp, KW, 2) <= (size_t)max_smem ? 2 : 1;
     const size_t smem = Syn2<S>::total(Kp, KW, nst);
-    syn2_kernel<S><<<grid, 256, smem, st>>>(im, K, Kp, KW, nst, bits, seg_base, packed, bsyn,
-                                            xcore, spill, err);
+    syn2_kernel<S><<<grid, 256, smem, st>>>(im, K, Kp, KW, nst, bits, seg_base, pxoff, packed,
+                                            bsyn, xcore, spill, err);
     return cudaGetLastError();
   });
 }
 
 cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
-                        const uint64_t *seg_base, float *packed, const uint4 *badj, const float *r,
-                        const StepParams *prm, int *err, int grid, cudaStream_t st) {
+                        const uint64_t *seg_base, const uint16_t *pxoff, float *packed,
+                        const uint4 *badj, const float *r, const StepParams *prm, int *err,
+                        int grid, cudaStream_t st) {
   const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
   return dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
     const size_t smem = Adj2<S>::total(Kp, KW);
-    adj2_kernel<S><<<grid, 256, smem, st>>>(im, K, Kp, KW, bits, seg_base, packed, badj, r, prm,
-                                            err);
+    adj2_kernel<S><<<grid, Adj2<S>::kThreads, smem, st>>>(im, K, Kp, KW, bits, seg_base, pxoff,
+                                                          packed, badj, r, prm, err);
     return cudaGetLastError();
   });
 }

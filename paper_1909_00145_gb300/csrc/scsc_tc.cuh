@@ -22,8 +22,8 @@ struct TuneKey {
 
 // Everything a captured iteration graph depends on.
 struct GraphKey {
-  const void *bits, *seg_base, *packed, *bsyn, *badj, *xcore, *spill, *r, *err, *x, *prm, *item0,
-      *off;
+  const void *bits, *seg_base, *pxoff, *packed, *bsyn, *badj, *xcore, *spill, *r, *err, *x, *prm,
+      *item0, *off;
   int K, s, Q, variant, iters;
 };
 
@@ -33,7 +33,7 @@ struct TcWorkspace {
     void *p = nullptr;
     size_t bytes = 0;
   };
-  Buf item0, seg_count, seg_base, scan_blocks, packed, xcore, spill, r, badj, bsyn, err;
+  Buf item0, seg_count, seg_base, pxoff, scan_blocks, packed, xcore, spill, r, badj, bsyn, err;
   std::vector<int> host_item0;  // cached row-item map of the last batch
   std::vector<int> host_H, host_W;
   int n_items = 0;
