@@ -436,9 +436,19 @@ struct Syn2 {
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)N * Kp * 2; }
   __host__ __device__ static size_t vals_bytes(int Kp) { return (size_t)kStrip * Kp * 4; }
   __host__ __device__ static size_t mask_bytes(int KW) { return (size_t)kStrip * KW * 4; }
-  __host__ __device__ static size_t total(int Kp, int KW, int nst) {
-    return 1024 + a_bytes(Kp) + b_bytes(Kp) + (size_t)nst * vals_bytes(Kp) +
+  // nst staging buffers of packed codes, nab A-operand buffers
+  __host__ __device__ static size_t total(int Kp, int KW, int nst, int nab) {
+    return 1024 + (size_t)nab * a_bytes(Kp) + b_bytes(Kp) + (size_t)nst * vals_bytes(Kp) +
            (size_t)2 * 4 * 2 * S * S * 4;
+  }
+  // the largest buffering that fits: (2, 2), else (2, 1), else (1, 1)
+  static void pick(int Kp, int KW, int max_smem, int &nst, int &nab) {
+    nst = 2;
+    nab = 2;
+    if (total(Kp, KW, nst, nab) <= (size_t)max_smem) return;
+    nab = 1;
+    if (total(Kp, KW, nst, nab) <= (size_t)max_smem) return;
+    nst = 1;
   }
 };
 
@@ -471,6 +481,7 @@ struct CodeRowGen {
 
 template <int S>
 __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp, int KW, int nst,
+                                                      int nab,
                                                       const uint32_t *__restrict__ bits,
                                                       const uint64_t *__restrict__ seg_base,
                                                       const uint16_t *__restrict__ pxoff,
@@ -483,8 +494,9 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
   const int NC = Kp / 16;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
-  uint8_t *As = smem;
-  uint8_t *Bs = As + L::a_bytes(Kp);
+  uint8_t *const As0 = smem;
+  uint8_t *const As1 = As0 + (nab == 2 ? L::a_bytes(Kp) : 0);
+  uint8_t *Bs = As1 + L::a_bytes(Kp);
   uint8_t *p = Bs + L::b_bytes(Kp);
   float *const vals0 = reinterpret_cast<float *>(p);
   p += L::vals_bytes(Kp);
@@ -496,7 +508,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
   auto vals = [&](int k) { return (k & 1) ? vals1 : vals0; };
   float *Pu = reinterpret_cast<float *>(p);  // edge exchange of the col2im, [2][4][2c][S]
 
-  __shared__ uint64_t tfull[2], tempty[2], stg_full[2], a_free, done_bar;
+  __shared__ uint64_t tfull[2], tempty[2], stg_full[2], a_free[2], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
@@ -511,7 +523,8 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
       tc::mbar_init(&tempty[i], 4);
       tc::mbar_init(&stg_full[i], 1);
     }
-    tc::mbar_init(&a_free, 1);
+    tc::mbar_init(&a_free[0], 1);
+    tc::mbar_init(&a_free[1], 1);
     tc::mbar_init(&done_bar, 1);
     abort_flag = 0;
     tc::fence_mbar_init();
@@ -536,7 +549,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     // ------------------------------------------------ producers + MMA issue
     const int e = tid;
     const uint32_t idesc = tc::idesc_bf16_f32(128, N);
-    const uint32_t a_base = tc::smem_u32(As), b_base = tc::smem_u32(Bs);
+    const uint32_t b_base = tc::smem_u32(Bs);
     const uint32_t b_lbo = 2 * S * 128;
     // code rows in sequence: g (current), nx (next), nn (after next); the
     // seg_base values of each row are loaded one iteration before they are used
@@ -578,9 +591,13 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
         load_masks(nx.sg.it, nx.a, KW, bits, pxoff, e, mwn, pon);
       }
       const uint32_t use = (uint32_t)(nst == 2 ? (i >> 1) : i);
+      // A buffer of this row; its previous user is row i - nab
+      const int ab = nab == 2 ? (i & 1) : 0;
+      uint8_t *const As = ab ? As1 : As0;
       bool okw = tc::mbar_wait_abortable(&stg_full[sb], use & 1u, abort_v, kWaitNs);
-      if (e == 0 && i > 0 && okw)
-        okw = tc::mbar_wait_abortable(&a_free, (uint32_t)((i - 1) & 1), abort_v, kWaitNs);
+      if (e == 0 && i >= nab && okw)
+        okw = tc::mbar_wait_abortable(&a_free[ab], (uint32_t)(((i - nab) / nab) & 1), abort_v,
+                                      kWaitNs);
       if (tc::named_sync_or(1, 128, !okw)) break;
       const float *dv = vals(sb);
       // running address of the pixel's next sampled value (filter order)
@@ -613,6 +630,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
                                            kWaitNs);
         if (okm) {
           tc::fence_after_sync();
+          const uint32_t a_base = tc::smem_u32(As);
 #pragma unroll 1
           for (int kk = 0; kk < NC; ++kk) {
             uint64_t ad = tc::smem_desc(a_base + kk * 2 * 2048, 2048, 128);
@@ -620,7 +638,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
             tc::mma_bf16(taddr + b * 256, ad, bd, idesc, kk > 0 ? 1u : 0u);
           }
           tc::mma_commit(&tfull[b]);
-          tc::mma_commit(&a_free);
+          tc::mma_commit(&a_free[ab]);
         }
       }
 #pragma unroll
@@ -642,15 +660,25 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     }
   } else {
     // ------------------------------------------------ epilogue: col2im
-    // Output column L of this warp gets sum_v P[L + c - v][(u, v)] by warp
-    // shuffles; contributions that cross a warp boundary are summed by the
-    // edge lanes (c lanes at each side) and exchanged once per code row; the
-    // strip's outer edges accumulate the spill columns.
+    // Output column L of this warp gets sum_v P[L + c - v][(u, v)] by one warp
+    // shuffle per tap from lane (L + c - v) mod 32.  A source index that wraps
+    // around the warp delivers a contribution to the neighbouring warp's
+    // column L (the left neighbour's when L + c - v >= 32, the right one's when
+    // it is < 0): those land on the c right-edge and c left-edge lanes, are
+    // exchanged once per code row, and at the strip's outer edges accumulate
+    // the spill columns.
     const int e = tid - 128, ew = e >> 5;
     const uint32_t lane_base = taddr + ((uint32_t)(32 * ew) << 16);
     const bool left_edge = lane < C, right_edge = lane >= 32 - C;
-    const bool spill_lane = (ew == 0 && left_edge) || (ew == 3 && right_edge);
-    const int spill_slot = ew == 0 ? lane : lane - 32 + 2 * C;
+    // taps v whose source lane L + c - v lies inside the warp (bit v)
+    uint32_t own_taps = 0u;
+#pragma unroll
+    for (int v = 0; v < S; ++v)
+      if ((unsigned)(lane + C - v) < 32u) own_taps |= 1u << v;
+    // spill slots: j < c = column b0 - c + j (warp 0, lane 32 - c + j),
+    // c + j = column b0 + 128 + j (warp 3, lane j)
+    const bool spill_lane = (ew == 0 && right_edge) || (ew == 3 && left_edge);
+    const int spill_slot = ew == 0 ? lane - (32 - C) : C + lane;
     SegIter sg{q_begin, q_end};
     int i = 0;
     bool ok = true;
@@ -688,15 +716,12 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
 #pragma unroll
           for (int v = 0; v < S; ++v) {
             const float pvv = __uint_as_float(pr[u % kB][v]);
-            const int so = lane + C - v;
-            const float t = __shfl_sync(0xffffffffu, pvv, so & 31);
-            const float tv = (so >= 0 && so < 32) ? t : 0.0f;
-            if (v & 1) own1 += tv;
-            else own0 += tv;
-            if (C > 0) {
-              const int sh = left_edge ? lane - v : lane + 2 * C - v;
-              const float th = __shfl_sync(0xffffffffu, pvv, sh & 31);
-              hal += (sh >= 0 && sh < 32) ? th : 0.0f;
+            const float t = __shfl_sync(0xffffffffu, pvv, (lane + C - v) & 31);
+            if ((own_taps >> v) & 1u) {
+              if (v & 1) own1 += t;
+              else own0 += t;
+            } else {
+              hal += t;
             }
           }
           acc[u] += own0 + own1;
@@ -706,11 +731,12 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&tempty[b]);
         if (C > 0) {
-          // edge partial sums: slot j < c = left halo column j - c (lane j),
-          // slot c + j = right halo column 32 + j (lane 32 - c + j)
+          // edge partial sums of warp ew: slot j < c = its left neighbour's
+          // column 32 - c + j (lane 32 - c + j), slot c + j = its right
+          // neighbour's column j (lane j)
           float *xb = Pu + (i & 1) * (4 * 2 * C * S);
           if (left_edge || right_edge) {
-            const int slot = left_edge ? lane : C + lane - (32 - C);
+            const int slot = right_edge ? lane - (32 - C) : C + lane;
 #pragma unroll
             for (int u = 0; u < S; ++u) xb[(ew * 2 * C + slot) * S + u] = hacc[u];
           }
@@ -783,7 +809,7 @@ bool tc_pipe_supported(int K, int s, int max_smem) {
   dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
     need = Adj2<S>::total(Kp, KW);
-    size_t syn = Syn2<S>::total(Kp, KW, 1);
+    size_t syn = Syn2<S>::total(Kp, KW, 1, 1);
     if (syn > need) need = syn;
     return cudaSuccess;
   });
@@ -796,9 +822,10 @@ cudaError_t prepare_pipe(int K, int s, int max_smem) {
   const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
   return dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
-    int nst = Syn2<S>::total(Kp, KW, 2) <= (size_t)max_smem ? 2 : 1;
+    int nst, nab;
+    Syn2<S>::pick(Kp, KW, max_smem, nst, nab);
     cudaError_t e = cudaFuncSetAttribute(syn2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Syn2<S>::total(Kp, KW, nst));
+                                         (int)Syn2<S>::total(Kp, KW, nst, nab));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(adj2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Adj2<S>::total(Kp, KW));
@@ -812,10 +839,11 @@ cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint32_t
   const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
   return dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
-    int nst = Syn2<S>::total(Kp, KW, 2) <= (size_t)max_smem ? 2 : 1;
-    const size_t smem = Syn2<S>::total(Kp, KW, nst);
-    syn2_kernel<S><<<grid, 256, smem, st>>>(im, K, Kp, KW, nst, bits, seg_base, pxoff, packed,
-                                            bsyn, xcore, spill, err);
+    int nst, nab;
+    Syn2<S>::pick(Kp, KW, max_smem, nst, nab);
+    const size_t smem = Syn2<S>::total(Kp, KW, nst, nab);
+    syn2_kernel<S><<<grid, 256, smem, st>>>(im, K, Kp, KW, nst, nab, bits, seg_base, pxoff,
+                                            packed, bsyn, xcore, spill, err);
     return cudaGetLastError();
   });
 }
