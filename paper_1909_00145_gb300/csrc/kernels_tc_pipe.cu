@@ -348,7 +348,10 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
       const int q = q_begin + i;
       const uint64_t b3v = seg_base[min(q + 3, Q)];
       if (i + 1 < n_items) {
-        if (e == 0) stage_item(b1v, b2v, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
+        if (e == 0) {
+          tc::bulk_wait_read0();  // item i - 1's write-back has left the buffer
+          stage_item(b1v, b2v, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
+        }
         load_masks(nxt, nxt.a, KW, bits, pxoff, px, mwn, pon);
       }
       // this pixel's first value of chunk c_lo inside the staged item
@@ -399,14 +402,16 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
         }
       }
       tc::fence_before_sync();
+      tc::fence_proxy_async();  // the updated codes, to the bulk copy below
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
       tc::named_sync(1, kE);
-      const int nv4 = (int)((b1v - b0v) >> 2);
-      for (int k = e; k < nv4; k += kE)
-        *reinterpret_cast<float4 *>(packed + b0v + 4 * (uint64_t)k) =
-            *reinterpret_cast<const float4 *>(dv + 4 * k);
-      tc::named_sync(1, kE);  // the buffer is refilled by the prefetch two items on
+      // write-back: one bulk copy; the thread that issues it waits for its
+      // reads before it refills this buffer (prefetch two items on)
+      if (e == 0 && b1v > b0v) {
+        tc::bulk_s2g(packed + b0v, dv, (uint32_t)(b1v - b0v) * 4u);
+        tc::bulk_commit();
+      }
 #pragma unroll
       for (int w = 0; w < 4; ++w) mw[w] = mwn[w];
       po = pon;
@@ -415,6 +420,7 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
       b2v = b3v;
       if (i + 2 < n_items) nxt = next_item(im, nxt);
     }
+    if (e == 0) tc::bulk_wait0();  // write-backs complete before the CTA exits
   }
 
   __syncthreads();
