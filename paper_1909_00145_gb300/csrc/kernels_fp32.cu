@@ -406,15 +406,15 @@ __global__ void power_init_kernel(float *u, int64_t n, uint64_t seed, uint64_t t
     u[i] = (splitmix64(base ^ (uint64_t)i) >> 63) ? -1.0f : 1.0f;
 }
 
-// u = w / ||w|| with ||w||^2 = sum of partials (fixed order); u = 0 if ||w|| = 0.
-__global__ void power_normalize_kernel(const float *w, float *u, int64_t n,
-                                       const double *partials, int nb) {
+// u = w / ||w|| with ||w||^2 = sum of partials (fixed order: strided per
+// thread, then the block tree); u = 0 if ||w|| = 0.
+__global__ void __launch_bounds__(256) power_normalize_kernel(const float *w, float *u, int64_t n,
+                                                              const double *partials, int nb) {
   __shared__ double inv;
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < nb; ++i) s += partials[i];
-    inv = s > 0.0 ? 1.0 / sqrt(s) : 0.0;
-  }
+  double p = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 256) p += partials[i];
+  p = block_sum<256>(p);
+  if (threadIdx.x == 0) inv = p > 0.0 ? 1.0 / sqrt(p) : 0.0;
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -425,9 +425,12 @@ __global__ void power_normalize_kernel(const float *w, float *u, int64_t n,
 // step = fixed_step if > 0 else 1 / L (0 when L = 0).
 __global__ void power_finish_kernel(const double *partials, int nb, double safety, double *L_out,
                                     double lambda, double fixed_step, StepParams *prm) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double s = 0.0;
-  for (int i = 0; i < nb; ++i) s += partials[i];
+  if (blockIdx.x != 0) return;
+  double s = 0.0;  // one warp, fixed order
+  for (int i = threadIdx.x; i < nb; i += 32) s += partials[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x != 0) return;
   double L = safety * s;
   if (L_out != nullptr) *L_out = L;
   if (prm != nullptr) {

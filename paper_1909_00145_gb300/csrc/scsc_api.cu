@@ -72,7 +72,8 @@ struct scsc_ctx {
   std::string err;
   BatchCache batch, domain;     // the call's batch; the step-size domain
   int domainH = -1, domainW = -1;
-  DevBuf bits, r, pix2, prm, scal, partials, gpart, gsum, pu, pw, pcodes, psplit, flag;
+  DevBuf bits, r, pix2, prm, scal, partials, gpart, gsum, pu, pw, flag;
+  DevBuf ddtG, ddtA;  // tap Gram matrix and per-class stencils of D D^T
   // tensor path
   TcWorkspace tc;
   // online surrogates
@@ -219,17 +220,13 @@ scsc_status build_mask(scsc_ctx *ctx, uint64_t t) {
   return SCSC_OK;
 }
 
-// Operator D D^T on the step-size domain: u (pixels) -> w (pixels).
-// A single image gives few 32x32 tiles, so the filters are split over blocks
-// until the launch has about two blocks per SM.
-scsc_status apply_ddt(scsc_ctx *ctx, const float *d, const float *u, float *w) {
-  const BatchDev &b = ctx->domain.view;
-  const int ksplit = std::max(1, std::min((304 + b.n_tiles - 1) / b.n_tiles, (ctx->cfg.K + 31) / 32));
-  CK(ctx->psplit.ensure((size_t)ksplit * b.total_px * 4));
-  CK(launch_adjoint_fp32(b, ctx->cfg.K, ctx->cfg.s, d, u, nullptr, 0, nullptr,
-                         ctx->pcodes.as<float>(), ctx->stream, ksplit));
-  CK(launch_synth_fp32(b, ctx->cfg.K, ctx->cfg.s, d, ctx->pcodes.as<float>(), nullptr, nullptr, w,
-                       ctx->stream, ksplit, ctx->psplit.as<float>()));
+// Operator D D^T on the step-size domain: u (pixels) -> w (pixels), through
+// the per-class stencils built from d by launch_ddt_prepare (the same linear
+// map as the adjoint followed by the synthesis, in (2s-1)^2 multiply-adds per
+// pixel instead of 2 K s^2).
+scsc_status apply_ddt(scsc_ctx *ctx, const float *u, float *w) {
+  CK(launch_ddt_apply(ctx->ddtA.as<float>(), ctx->cfg.s, ctx->domainH, ctx->domainW, u, w,
+                      ctx->stream));
   return SCSC_OK;
 }
 
@@ -303,10 +300,14 @@ scsc_status code_step_size(scsc_ctx *ctx, const float *d) {
     ctx->domainH = H;
     ctx->domainW = W;
   }
-  CK(ctx->pcodes.ensure((size_t)H * W * ctx->cfg.K * 4));
+  const int sz = ctx->cfg.s;
+  CK(ctx->ddtG.ensure((size_t)sz * sz * sz * sz * 8));
+  CK(ctx->ddtA.ensure(ddt_stencil_floats(sz, H, W) * 4));
   int pr = ctx->prof.begin(KID_POWER, ctx->stream);
+  CK(launch_ddt_prepare(d, ctx->cfg.K, sz, H, W, ctx->ddtG.as<double>(), ctx->ddtA.as<float>(),
+                        ctx->stream));
   scsc_status s = power_iteration(
-      ctx, (int64_t)H * W, kTagLz, [&](const float *u, float *w) { return apply_ddt(ctx, d, u, w); },
+      ctx, (int64_t)H * W, kTagLz, [&](const float *u, float *w) { return apply_ddt(ctx, u, w); },
       0, prm, 0.0);
   ctx->prof.end(pr, ctx->stream);
   return s;
@@ -361,8 +362,8 @@ scsc_status scsc_destroy(scsc_ctx *ctx) {
   if (!ctx) return SCSC_OK;
   cudaStreamSynchronize(ctx->stream);
   for (DevBuf *b : {&ctx->bits, &ctx->r, &ctx->pix2, &ctx->prm, &ctx->scal, &ctx->partials,
-                    &ctx->gpart, &ctx->gsum, &ctx->pu, &ctx->pw, &ctx->pcodes, &ctx->psplit,
-                    &ctx->flag,
+                    &ctx->gpart, &ctx->gsum, &ctx->pu, &ctx->pw,
+                    &ctx->flag, &ctx->ddtG, &ctx->ddtA,
                     &ctx->C, &ctx->B, &ctx->Cd, &ctx->batch.dev, &ctx->domain.dev})
     b->release();
   for (BatchCache *bc : {&ctx->batch, &ctx->domain}) {

@@ -91,6 +91,14 @@ cudaError_t launch_sum_sq_abs(const float *a, int64_t n_sq, const float *b, int6
                               double *partials, int n_blocks, cudaStream_t st);
 cudaError_t launch_finish_sum(const double *partials, int n_blocks, double scale_sq,
                               double scale_abs, double *out, cudaStream_t st);
+// D D^T of the step-size domain as per-class stencils (kernels_ddt.cu):
+// prepare builds the tap Gram matrix G (FP64, (s*s)^2) and the stencils A
+// (ddt_stencil_floats(s, H, W) floats) from d; apply computes w = D D^T u.
+size_t ddt_stencil_floats(int s, int H, int W);
+cudaError_t launch_ddt_prepare(const float *d, int K, int s, int H, int W, double *G, float *A,
+                               cudaStream_t st);
+cudaError_t launch_ddt_apply(const float *A, int s, int H, int W, const float *u, float *w,
+                             cudaStream_t st);
 cudaError_t launch_power_init(float *u, int64_t n, uint64_t seed, uint64_t tag, cudaStream_t st);
 cudaError_t launch_dot_partials(const float *a, const float *b, int64_t n, double *partials,
                                 int n_blocks, cudaStream_t st);

@@ -98,9 +98,22 @@ def test_lipschitz_and_objective_fp32():
     ctx = scsc.Context(K, s, lam=0.7, seed=21)
     b = scsc.Batch(H, W)
     L = ctx.lipschitz_codes(b, dev(d))
-    assert L == pytest.approx(R.lipschitz_codes(cfg, d, max(H), max(W)), rel=1e-4)
+    assert L == pytest.approx(R.lipschitz_codes(cfg, d, max(H), max(W)), rel=2e-5)
     f = ctx.objective(b, dev(x), dev(z), dev(d))
     assert f == pytest.approx(R.objective(cfg, rb, x, z, d), rel=1e-6)
+
+
+@pytest.mark.parametrize("s,H,W", [(11, 7, 9), (11, 11, 30), (11, 12, 257), (5, 40, 3),
+                                   (7, 96, 128), (1, 5, 6)])
+def test_step_size_operator_on_small_and_ragged_domains(s, H, W):
+    """L_z comes from the per-class stencil form of D D^T: domains smaller than
+    the filter (every row its own boundary class), exactly 2c+1, ragged."""
+    K = 12
+    d = make_case([H], [W], K, s, seed=5)[1]
+    cfg = R.Config(K=K, s=s, lam=1.0, seed=33)
+    ctx = scsc.Context(K, s, lam=1.0, seed=33)
+    L = ctx.lipschitz_codes(scsc.Batch([H], [W]), dev(d))
+    assert L == pytest.approx(R.lipschitz_codes(cfg, d, H, W), rel=2e-5)
 
 
 # ------------------------------------------------------------------ code step
