@@ -143,10 +143,11 @@ def measured_traffic(kernel: str, npx: int):
 
 def launches_per_step(path: str, n_iters: int) -> int:
     """Kernels the library launches in one scsc_code_step (counted from the
-    host orchestration): mask 1; power iteration 3 + 50 * 4 + 4; then
+    host orchestration): mask 1; step size: stencils 2, power iteration
+    3 + 50 * 3 + 3; then
     plain: apply-mask 1 + 2 per iteration;
     tensor: filter images 1, segment counts 1, scan 3, pack 1, 3 per iteration, unpack 1."""
-    base = 1 + (3 + 50 * 4 + 4)
+    base = 1 + 2 + (3 + 50 * 3 + 3)
     if path == "fp32":
         return base + 1 + 2 * n_iters
     return base + 1 + 1 + 3 + 1 + 3 * n_iters + 1
