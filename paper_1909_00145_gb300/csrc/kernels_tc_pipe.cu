@@ -1,18 +1,22 @@
 // kernels_tc_pipe.cu -- warp-specialised, pipelined tcgen05 kernels of the
-// code update for K <= 128 (one persistent CTA per SM, 8 warps).
+// code update for K <= 128 (one persistent CTA per SM).
 //
-// Adjoint + prox (Eq. 3): warps 1-3 build the Toeplitz BF16 rows of the
-// residual into a ring of shared-memory slots (residual rows fetched with
-// cp.async two rows ahead); warp 0 issues, per item, one MMA per tap row into
-// one of two TMEM accumulators; warps 4-7 prefetch the next item's packed
-// codes and mask words with cp.async, apply the soft-threshold step to the
-// sampled coordinates from the accumulator and write the item back.
+// Adjoint + prox (Eq. 3), 12 warps: warps 1-3 fetch residual rows with
+// cp.async and write each as 8 shifted BF16 copies (a Toeplitz view) into a
+// 16-slot shared-memory ring; warp 0 (lane 0) issues, per row item, one MMA
+// per tap row into one of two TMEM accumulators; warps 4-11 are two epilogue
+// groups of four warps (each covers all 128 pixels of the item and half of its
+// filter chunks): they prefetch the next item's packed codes with one bulk
+// copy and its mask words and pixel offsets into registers, apply the
+// soft-threshold step to the sampled coordinates and write the item back with
+// one bulk copy.
 //
-// Synthesis: warps 0-3 prefetch packed codes and masks with cp.async, expand
-// them into the BF16 A operand and (thread 0) issue the MMAs P = Z D^T into
-// one of two TMEM accumulators; warps 4-7 fold P into output rows (col2im)
-// through a small shared-memory transpose and write the strip's core columns
-// and its 2c spill columns.
+// Synthesis, 8 warps: warps 0-3 expand the staged packed codes of a code row
+// into the BF16 A operand (two buffers when shared memory allows) and thread 0
+// issues the MMAs P = Z D^T into one of two TMEM accumulators; warps 4-7 fold
+// P into output rows (col2im by warp shuffles, the warp-edge halo exchanged
+// through shared memory) and write the strip's core columns and its 2c spill
+// columns.
 //
 // Every wait is bounded; on timeout the CTA raises an abort flag, all roles
 // leave their loops, the MMAs already issued are waited for (bounded) and the
