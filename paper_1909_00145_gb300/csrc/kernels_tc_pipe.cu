@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
   auto vals = [&](int k) { return (k & 1) ? vals1 : vals0; };
   float *Pu = reinterpret_cast<float *>(p);  // edge exchange of the col2im, [2][4][2c][S]
 
-  __shared__ uint64_t tfull[2], tempty[2], stg_full[2], a_free[2], done_bar;
+  __shared__ uint64_t tfull[2], stg_full[2], a_full[2], a_free[2], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
@@ -530,11 +530,10 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&tfull[i], 1);
-      tc::mbar_init(&tempty[i], 4);
       tc::mbar_init(&stg_full[i], 1);
+      tc::mbar_init(&a_full[i], 4);  // one arrival per expanding warp
+      tc::mbar_init(&a_free[i], 1);
     }
-    tc::mbar_init(&a_free[0], 1);
-    tc::mbar_init(&a_free[1], 1);
     tc::mbar_init(&done_bar, 1);
     abort_flag = 0;
     tc::fence_mbar_init();
@@ -555,12 +554,12 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
   const int q_end = (int)((int64_t)Q * (blockIdx.x + 1) / gridDim.x);
   volatile int *abort_v = &abort_flag;
 
+  auto a_buf = [&](int r) { return (nab == 2 && (r & 1)) ? As1 : As0; };
   if (warp < 4) {
-    // ------------------------------------------------ producers + MMA issue
+    // ------------------------------------------------ expand
+    // Each warp runs on its own mbarrier waits (lane 0 waits, the warp
+    // follows) and signals a_full when its 32 pixels of the row are in A.
     const int e = tid;
-    const uint32_t idesc = tc::idesc_bf16_f32(128, N);
-    const uint32_t b_base = tc::smem_u32(Bs);
-    const uint32_t b_lbo = 2 * S * 128;
     // code rows in sequence: g (current), nx (next), nn (after next); the
     // seg_base values of each row are loaded one iteration before they are used
     auto base_of = [&](int qq) { return seg_base[qq]; };
@@ -569,11 +568,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     bool have = g.next(im);
     CodeRowGen nx = g;
     bool have_nx = have && nx.next(im);
-    uint64_t gb0 = 0, gb1 = 0, nb0 = 0, nb1 = 0;
-    if (have) {
-      gb0 = base_of(g.q());
-      gb1 = base_of(g.q() + 1);
-    }
+    uint64_t nb0 = 0, nb1 = 0;
     if (have_nx) {
       nb0 = base_of(nx.q());
       nb1 = base_of(nx.q() + 1);
@@ -582,7 +577,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     // single buffer); mask words: registers, loaded one row ahead
     uint32_t mw[4], mwn[4], po = 0, pon = 0;
     if (have) {
-      if (e == 0) stage_item(gb0, gb1, packed, vals(0), &stg_full[0]);
+      if (e == 0) stage_item(base_of(g.q()), base_of(g.q() + 1), packed, vals(0), &stg_full[0]);
       load_masks(g.sg.it, g.a, KW, bits, pxoff, e, mw, po);
     }
     int i = 0;
@@ -595,21 +590,31 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
         mb1 = base_of(nn.q() + 1);
       }
       const int sb = nst == 2 ? (i & 1) : 0;
+      const int ab = nab == 2 ? (i & 1) : 0;
+      bool w = true;
       if (have_nx) {
-        if (nst == 2 && e == 0)
-          stage_item(nb0, nb1, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
+        // two staging buffers: row i + 1 replaces row i - 1 once all four
+        // warps have expanded it
+        if (nst == 2 && e == 0) {
+          if (i >= 1) {
+            const int pb = nab == 2 ? ((i - 1) & 1) : 0;
+            w = tc::mbar_wait_abortable(&a_full[pb], (uint32_t)(((i - 1) / nab) & 1), abort_v,
+                                        kWaitNs);
+          }
+          if (w) stage_item(nb0, nb1, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
+        }
         load_masks(nx.sg.it, nx.a, KW, bits, pxoff, e, mwn, pon);
       }
-      const uint32_t use = (uint32_t)(nst == 2 ? (i >> 1) : i);
-      // A buffer of this row; its previous user is row i - nab
-      const int ab = nab == 2 ? (i & 1) : 0;
-      uint8_t *const As = ab ? As1 : As0;
-      bool okw = tc::mbar_wait_abortable(&stg_full[sb], use & 1u, abort_v, kWaitNs);
-      if (e == 0 && i >= nab && okw)
-        okw = tc::mbar_wait_abortable(&a_free[ab], (uint32_t)(((i - nab) / nab) & 1), abort_v,
+      if (lane == 0 && w) {
+        w = tc::mbar_wait_abortable(&stg_full[sb], (uint32_t)((nst == 2 ? (i >> 1) : i) & 1),
+                                    abort_v, kWaitNs);
+        if (w && i >= nab)
+          w = tc::mbar_wait_abortable(&a_free[ab], (uint32_t)(((i - nab) / nab) & 1), abort_v,
                                       kWaitNs);
-      if (tc::named_sync_or(1, 128, !okw)) break;
+      }
+      if (!__shfl_sync(0xffffffffu, w, 0)) break;
       const float *dv = vals(sb);
+      uint8_t *const As = a_buf(i);
       // running address of the pixel's next sampled value (filter order)
       uint32_t a_run = tc::smem_u32(dv) + 4u * po;
 #pragma unroll
@@ -632,41 +637,23 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
         *reinterpret_cast<uint4 *>(dst + 2048) = hi;
       }
       tc::fence_proxy_async();
-      tc::named_sync(1, 128);
-      if (nst == 1 && have_nx && e == 0) stage_item(nb0, nb1, packed, vals(0), &stg_full[0]);
-      if (e == 0) {
-        const int b = i & 1;
-        bool okm = tc::mbar_wait_abortable(&tempty[b], (uint32_t)(((i >> 1) & 1) ^ 1), abort_v,
-                                           kWaitNs);
-        if (okm) {
-          tc::fence_after_sync();
-          const uint32_t a_base = tc::smem_u32(As);
-#pragma unroll 1
-          for (int kk = 0; kk < NC; ++kk) {
-            uint64_t ad = tc::smem_desc(a_base + kk * 2 * 2048, 2048, 128);
-            uint64_t bd = tc::smem_desc(b_base + kk * 2 * b_lbo, b_lbo, 128);
-            tc::mma_bf16(taddr + b * 256, ad, bd, idesc, kk > 0 ? 1u : 0u);
-          }
-          tc::mma_commit(&tfull[b]);
-          tc::mma_commit(&a_free[ab]);
-        }
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&a_full[ab]);
+      if (nst == 1 && have_nx && e == 0) {
+        // one staging buffer: row i + 1 replaces row i once it is expanded
+        if (tc::mbar_wait_abortable(&a_full[ab], (uint32_t)((i / nab) & 1), abort_v, kWaitNs))
+          stage_item(nb0, nb1, packed, vals(0), &stg_full[0]);
       }
 #pragma unroll
-      for (int w = 0; w < 4; ++w) mw[w] = mwn[w];
+      for (int w2 = 0; w2 < 4; ++w2) mw[w2] = mwn[w2];
       po = pon;
       g = nx;
       have = have_nx;
-      gb0 = nb0;
-      gb1 = nb1;
       nx = nn;
       have_nx = have_nn;
       nb0 = mb0;
       nb1 = mb1;
       ++i;
-    }
-    if (tid == 0) {
-      tc::mma_commit(&done_bar);
-      tc::mbar_wait_bounded(&done_bar, 0, kWaitNs);
     }
   } else {
     // ------------------------------------------------ epilogue: col2im
@@ -689,9 +676,39 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     // c + j = column b0 + 128 + j (warp 3, lane j)
     const bool spill_lane = (ew == 0 && right_edge) || (ew == 3 && left_edge);
     const int spill_slot = ew == 0 ? lane - (32 - C) : C + lane;
+    // MMA issue (thread e = 0), one code row ahead of the col2im: P = Z D^T of
+    // row r into TMEM buffer r & 1 once the four expanding warps are done.
+    // The buffer's previous row was folded by this group before the group
+    // barrier that precedes the issue, so no TMEM-empty barrier is needed.
+    const uint32_t idesc = tc::idesc_bf16_f32(128, N);
+    const uint32_t b_base = tc::smem_u32(Bs);
+    const uint32_t b_lbo = 2 * S * 128;
+    auto issue = [&](int r) -> bool {
+      const int ab = nab == 2 ? (r & 1) : 0;
+      if (!tc::mbar_wait_abortable(&a_full[ab], (uint32_t)((r / nab) & 1), abort_v, kWaitNs))
+        return false;
+      tc::fence_after_sync();
+      const uint32_t a_base = tc::smem_u32(a_buf(r));
+#pragma unroll 1
+      for (int kk = 0; kk < NC; ++kk) {
+        uint64_t ad = tc::smem_desc(a_base + kk * 2 * 2048, 2048, 128);
+        uint64_t bd = tc::smem_desc(b_base + kk * 2 * b_lbo, b_lbo, 128);
+        tc::mma_bf16(taddr + (r & 1) * 256, ad, bd, idesc, kk > 0 ? 1u : 0u);
+      }
+      tc::mma_commit(&tfull[r & 1]);
+      tc::mma_commit(&a_free[ab]);
+      return true;
+    };
+    int n_rows = 0;  // code rows of this CTA
+    {
+      SegIter cnt{q_begin, q_end};
+      while (cnt.next(im)) n_rows += min(cnt.it.H, cnt.o1 + C) - max(0, cnt.o0 - C);
+    }
+    bool ok = true;
+    if (e == 0 && n_rows > 0) ok = issue(0);
+    ok = !tc::named_sync_or(2, 128, !ok);  // the group leaves together on a failed wait
     SegIter sg{q_begin, q_end};
     int i = 0;
-    bool ok = true;
     while (ok && sg.next(im)) {
       const int a_start = max(0, sg.o0 - C), a_end = min(sg.it.H, sg.o1 + C);
       const int b0 = sg.it.js * kStrip;
@@ -701,9 +718,12 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
       for (int u = 0; u < S; ++u) acc[u] = acch[u] = 0.0f;
       for (int a = a_start; a < a_end; ++a, ++i) {
         const int b = i & 1;
-        bool okw = true;
-        if (e == 0)
-          okw = tc::mbar_wait_abortable(&tfull[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
+        bool okw = ok;
+        if (e == 0) {
+          if (okw && i + 1 < n_rows) okw = issue(i + 1);
+          if (okw)
+            okw = tc::mbar_wait_abortable(&tfull[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
+        }
         if (tc::named_sync_or(2, 128, !okw)) {
           ok = false;
           break;
@@ -737,9 +757,10 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
           acc[u] += own0 + own1;
           hacc[u] = hal;
         }
+        // TMEM reads of this row end before the group barrier below, after
+        // which thread 0 may overwrite the buffer (row i + 2)
         tc::fence_before_sync();
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&tempty[b]);
+        if (C == 0) tc::named_sync(2, 128);
         if (C > 0) {
           // edge partial sums of warp ew: slot j < c = its left neighbour's
           // column 32 - c + j (lane 32 - c + j), slot c + j = its right
@@ -785,6 +806,10 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
           if (spill_lane) spill[(int64_t)(it.q_row0 + o) * (2 * C) + spill_slot] = acch[j];
         }
       }
+    }
+    if (e == 0) {  // the MMAs issued are complete before the TMEM is released
+      tc::mma_commit(&done_bar);
+      tc::mbar_wait_bounded(&done_bar, 0, kWaitNs);
     }
   }
 
