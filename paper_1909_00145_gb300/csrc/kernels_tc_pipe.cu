@@ -12,11 +12,11 @@
 // one bulk copy.
 //
 // Synthesis, 8 warps: warps 0-3 expand the staged packed codes of a code row
-// into the BF16 A operand (two buffers when shared memory allows) and thread 0
-// issues the MMAs P = Z D^T into one of two TMEM accumulators; warps 4-7 fold
-// P into output rows (col2im by warp shuffles, the warp-edge halo exchanged
-// through shared memory) and write the strip's core columns and its 2c spill
-// columns.
+// into the BF16 A operand (two buffers when shared memory allows); warps 4-7
+// fold P = Z D^T into output rows (col2im by warp shuffles, the warp-edge halo
+// exchanged through shared memory) and write the strip's core columns and its
+// 2c spill columns; their first thread issues the MMAs of the next code row
+// into the other of two TMEM accumulators before folding the current one.
 //
 // Every wait is bounded; on timeout the CTA raises an abort flag, all roles
 // leave their loops, the MMAs already issued are waited for (bounded) and the
