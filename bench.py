@@ -211,6 +211,57 @@ def run_reference(args, wl):
     print(json.dumps(out), flush=True)
 
 
+def accuracy_report(n_images=4):
+    """Errors of the BF16 and plain-FP32 paths against the FP64 oracle on the
+    first images of the 64 x 256^2 workload: one outer iteration (100 PG
+    iterations with the computed step) and one batch dictionary step; codes
+    and filters as relative L2 errors, the objective (Eq. 1) after each step
+    as a relative error.  One JSON line."""
+    import time
+    import torch
+    from oracle import reference as R
+    from paper_1909_00145_gb300 import scsc
+    wl = dict(WORKLOADS["c3"], n=n_images)
+    H, W, ids, x, d = make_inputs(wl, 0)
+    K, n_iters = wl["K"], wl["n_iters"]
+    cfg = R.Config(K=K, s=11, lam=1.0, p_num=wl["p"][0], p_den=wl["p"][1], seed=0)
+    rb = R.Batch(H=H, W=W, ids=ids)
+    t0 = time.perf_counter()
+    zo = R.code_step(cfg, rb, x, d, np.zeros(rb.total_pixels * K), 1, n_iters)
+    fzo = R.objective(cfg, rb, x, zo, d)
+    do = R.dict_step_batch(cfg, rb, x, zo, d)
+    fdo = R.objective(cfg, rb, x, zo, do)
+    oracle_s = time.perf_counter() - t0
+
+    def rel(a, b):
+        a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    out = {}
+    for prec in ["bf16", "fp32"]:
+        ctx = scsc.Context(K, 11, 1.0, wl["p"], seed=0, prec=prec, stream=torch.cuda.Stream())
+        batch = scsc.Batch(H, W, ids)
+        xt = torch.from_numpy(x).cuda()
+        dt = torch.from_numpy(np.ascontiguousarray(d)).cuda()
+        z = torch.zeros(batch.total_pixels * K, device="cuda")
+        torch.cuda.synchronize()
+        with torch.cuda.stream(ctx.stream):
+            ctx.code_step(batch, xt, dt, z, 1, n_iters)
+            fz = ctx.objective(batch, xt, z, dt)
+            ctx.dict_step(batch, xt, z, dt, scsc.SCSC_DICT_BATCH, 1)
+            fd = ctx.objective(batch, xt, z, dt)
+            ctx.sync()
+        out[prec] = {"codes_rel_l2": rel(z.cpu().numpy(), zo),
+                     "objective_after_codes_rel": abs(fz - fzo) / abs(fzo),
+                     "filters_rel_l2": rel(dt.cpu().numpy(), do),
+                     "objective_after_dict_rel": abs(fd - fdo) / abs(fdo)}
+        ctx.close()
+    print(json.dumps({"accuracy": out, "reference": "FP64 oracle",
+                      "workload": f"{n_images} x 256x256 of the 64-image workload, K=100, p=1/4, "
+                                  f"100 PG its + 1 batch dictionary step",
+                      "oracle_seconds": oracle_s}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -227,7 +278,12 @@ def main():
                     help="tensor path: always use the pipelined kernels (for profiler captures)")
     ap.add_argument("--no-graph", action="store_true",
                     help="tensor path: launch iterations directly instead of replaying a graph")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="print the BF16 / FP32 errors against the FP64 oracle on 4 images and exit")
     args = ap.parse_args()
+    if args.accuracy:
+        accuracy_report()
+        return
     if args.warmup < 3:
         args.warmup = 3
     wl = WORKLOADS[args.workload]
