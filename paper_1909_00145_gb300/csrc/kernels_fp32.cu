@@ -40,25 +40,29 @@ __device__ __forceinline__ bool bit_of(const uint32_t *bits, int64_t pix, int KW
 
 // ------------------------------------------------------------------ mask
 
-__global__ void mask_bits_kernel(BatchDev b, int K, int KW, uint64_t seed, uint64_t t,
-                                 uint64_t T, uint32_t *bits) {
-  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= b.total_px * KW) return;
-  int64_t pix = g / KW;
-  int w = (int)(g - pix * KW);
-  int n = upper_index(b.off, b.n, pix);
-  int64_t local = pix - b.off[n];
-  int H = b.H[n], W = b.W[n];
-  int y = (int)(local / W), x = (int)(local - (int64_t)y * W);
-  uint64_t pre = mask_prefix(seed, t, (uint64_t)b.ids[n]);
-  uint32_t word = 0;
-  for (int j = 0; j < 32; ++j) {
-    int k = w * 32 + j;
-    if (k >= K) break;
-    uint64_t idx = ((uint64_t)k * (uint64_t)H + (uint64_t)y) * (uint64_t)W + (uint64_t)x;
-    if ((splitmix64(pre ^ idx) >> 32) < T) word |= 1u << j;
+// One block per 32x32 tile (image and position found once per block), one
+// thread per pixel column and every eighth row; the coordinate index
+// (k H + y) W + x advances by H W per filter.
+__global__ void __launch_bounds__(256) mask_bits_kernel(BatchDev b, int K, int KW, uint64_t seed,
+                                                        uint64_t t, uint64_t T, uint32_t *bits) {
+  const TileCoord tc = tile_coord(b, blockIdx.x);
+  const uint64_t pre = mask_prefix(seed, t, (uint64_t)b.ids[tc.n]);
+  const uint64_t HW = (uint64_t)tc.H * (uint64_t)tc.W;
+  const int x = tc.x0 + (threadIdx.x & 31);
+  if (x >= tc.W) return;
+  for (int yy = threadIdx.x >> 5; yy < kTile; yy += 8) {
+    const int y = tc.y0 + yy;
+    if (y >= tc.H) break;
+    const int64_t pix = tc.base + (int64_t)y * tc.W + x;
+    uint64_t idx = (uint64_t)y * (uint64_t)tc.W + (uint64_t)x;
+    for (int w = 0; w < KW; ++w) {
+      uint32_t word = 0;
+      const int kn = min(32, K - 32 * w);
+      for (int j = 0; j < kn; ++j, idx += HW)
+        if ((splitmix64(pre ^ idx) >> 32) < T) word |= 1u << j;
+      bits[pix * KW + w] = word;
+    }
   }
-  bits[g] = word;
 }
 
 __global__ void apply_mask_dense_kernel(int64_t total, int K, int KW, const uint32_t *bits,
@@ -516,10 +520,8 @@ inline int grid_for(int64_t n, int bs, int cap = 1 << 20) {
 cudaError_t launch_mask_bits(const BatchDev &b, int K, uint64_t seed, uint64_t t, uint64_t T,
                              uint32_t *bits, cudaStream_t st) {
   int KW = (K + 31) / 32;
-  int64_t n = b.total_px * KW;
-  if (n == 0) return cudaSuccess;
-  int64_t g = (n + 255) / 256;
-  mask_bits_kernel<<<(unsigned)g, 256, 0, st>>>(b, K, KW, seed, t, T, bits);
+  if (b.total_px == 0 || b.n_tiles == 0) return cudaSuccess;
+  mask_bits_kernel<<<b.n_tiles, 256, 0, st>>>(b, K, KW, seed, t, T, bits);
   return cudaGetLastError();
 }
 

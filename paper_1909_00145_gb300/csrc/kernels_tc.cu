@@ -159,8 +159,11 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int K
   const int npx = min(kStrip, it.W - it.js * kStrip);
   float *zb = z + (it.base + (int64_t)it.a * it.W + it.js * kStrip) * K;
   const int n = npx * K;
+  // (pixel, filter) of element j, advanced by kThreads elements per step
+  // without a division
+  int pl = threadIdx.x / K, k = threadIdx.x - pl * K;
+  const int dpl = kThreads / K, dk = kThreads - dpl * K;
   for (int j = threadIdx.x; j < n; j += kThreads) {
-    const int pl = j / K, k = j - pl * K;
     const int c = k >> 4, e = k & 15;
     const uint32_t m = s_m[c][pl];
     if ((m >> e) & 1u) {
@@ -169,6 +172,12 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int K
       else zb[j] = packed[idx];
     } else if (mode == 1) {
       zb[j] = 0.0f;
+    }
+    pl += dpl;
+    k += dk;
+    if (k >= K) {
+      k -= K;
+      ++pl;
     }
   }
 }
@@ -350,21 +359,35 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
 }
 
 // r = xcore + spills of the neighbouring strips - x
-__global__ void finalize_r_kernel(BatchDev b, ItemMap im, int C, const float *__restrict__ xcore,
-                                  const float *__restrict__ spill, const float *__restrict__ x,
-                                  float *__restrict__ r) {
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < b.total_px;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    int n = upper_index(b.off, b.n, p);
-    int64_t local = p - b.off[n];
-    int W = b.W[n], H = b.H[n];
-    int o = (int)(local / W), col = (int)(local - (int64_t)o * W);
-    int js = col / kStrip, lc = col - js * kStrip, JS = (W + kStrip - 1) / kStrip;
+// Each block takes a contiguous range of row items (image n, strip js, row
+// a); thread = column of the strip.  The first item is found by search, the
+// next ones by stepping the row (and, at a strip's end, a search).
+__global__ void __launch_bounds__(kThreads) finalize_r_kernel(ItemMap im, int C,
+                                                              const float *__restrict__ xcore,
+                                                              const float *__restrict__ spill,
+                                                              const float *__restrict__ x,
+                                                              float *__restrict__ r) {
+  const int q_begin = (int)((int64_t)im.total * blockIdx.x / gridDim.x);
+  const int q_end = (int)((int64_t)im.total * (blockIdx.x + 1) / gridDim.x);
+  if (q_begin >= q_end) return;
+  Item it = item_of(im, q_begin);
+  const int lc = threadIdx.x;
+  for (int q = q_begin; q < q_end; ++q) {
+    if (q > q_begin) {
+      if (it.a + 1 < it.H) {
+        ++it.a;
+      } else {
+        it = item_of(im, q);
+      }
+    }
+    const int col = it.js * kStrip + lc;
+    if (col >= it.W) continue;
+    const int64_t p = it.base + (int64_t)it.a * it.W + col;
     float v = xcore[p];
     if (C > 0) {
-      if (lc < C && js > 0) v += spill[(int64_t)(im.item0[n] + (js - 1) * H + o) * (2 * C) + C + lc];
-      if (lc >= kStrip - C && js + 1 < JS)
-        v += spill[(int64_t)(im.item0[n] + (js + 1) * H + o) * (2 * C) + lc - (kStrip - C)];
+      if (lc < C && it.js > 0) v += spill[(int64_t)(q - it.H) * (2 * C) + C + lc];
+      if (lc >= kStrip - C && it.js + 1 < it.JS)
+        v += spill[(int64_t)(q + it.H) * (2 * C) + lc - (kStrip - C)];
     }
     r[p] = v - x[p];
   }
@@ -738,7 +761,7 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
     TRY(cudaDeviceGetAttribute(&ws.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   }
   const bool pipe_ok = tc_pipe_supported(K, s, ws.max_smem);
-  const int fin_grid = (int)std::min<int64_t>((b.total_px + 255) / 256, 152 * 16);
+  const int fin_grid = std::min(Q, ws.sm_count * 16);  // finalize: blocks over row items
   // launch geometry of the single-stage kernels (several CTAs per SM)
   int grid_s1 = 1, grid_a1 = 1;
   size_t smem_s1 = 0, smem_a1 = 0;
@@ -783,8 +806,8 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
     }
     if (ws.prof) ws.prof->end(p1, st);
     int p2 = ws.prof ? ws.prof->begin(KID_FINALIZE, st) : -1;
-    finalize_r_kernel<<<fin_grid, 256, 0, st>>>(b, im, C, as<float>(ws.xcore), as<float>(ws.spill),
-                                                 x, as<float>(ws.r));
+    finalize_r_kernel<<<fin_grid, kThreads, 0, st>>>(im, C, as<float>(ws.xcore), as<float>(ws.spill),
+                                                      x, as<float>(ws.r));
     TRY(cudaGetLastError());
     if (ws.prof) ws.prof->end(p2, st);
     int p3 = ws.prof ? ws.prof->begin(KID_ADJ_TC, st) : -1;
