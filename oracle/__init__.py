@@ -64,6 +64,9 @@ def lib() -> ctypes.CDLL:
                 "orc_project_filters": (None, [i, i, P]),
                 "orc_objective_image": (dbl, [i, i, i, i, P, P, P, dbl]),
                 "orc_code_update_image": (None, [i, i, i, i, P, P, P, P, dbl, dbl, i]),
+                "orc_objective_image_observed": (dbl, [i, i, i, i, P, P, P, P, dbl]),
+                "orc_code_update_image_observed": (None, [i, i, i, i, P, P, P, P, P, dbl, dbl,
+                                                          i]),
                 "orc_power_ddt": (dbl, [i, i, i, i, P, u64, u64, i]),
                 "orc_power_ztz": (dbl, [i, P, P, P, i, i, P, u64, u64, i]),
                 "orc_power_dense": (dbl, [i, P, u64, u64, i]),

@@ -190,6 +190,47 @@ def code_step(cfg: Config, batch: Batch, x, d, z, t: int, n_iters: int,
     return z
 
 
+def objective_observed(cfg: Config, batch: Batch, x, z, d, obs) -> float:
+    """Eq. 1 with the data term over observed pixels only (inpainting, Sec.
+    4.3); obs: one 0/1 byte per pixel of the batch."""
+    x, z, d = _f64(x), _f64(z), _f64(d)
+    obs = np.ascontiguousarray(obs, dtype=np.uint8).ravel()
+    tot = 0.0
+    for n in range(batch.n):
+        H, W = int(batch.H[n]), int(batch.W[n])
+        tot += lib().orc_objective_image_observed(
+            cfg.K, cfg.s, H, W, _p(d), _p(np.ascontiguousarray(batch.image(z, n, cfg.K))),
+            _p(np.ascontiguousarray(batch.image(x, n))),
+            _p(np.ascontiguousarray(batch.image(obs, n))), cfg.lam)
+    return float(tot)
+
+
+def code_step_observed(cfg: Config, batch: Batch, x, d, z, obs, t: int, n_iters: int,
+                       step: float | None = None) -> np.ndarray:
+    """code_step with the data term over observed pixels only (inpainting,
+    Sec. 4.3).  The step is 1/L_z of the unmasked operator unless given: a
+    valid step, since ||O D|| <= ||D|| for the 0/1 diagonal O."""
+    x, d = _f64(x), _f64(d)
+    z = _f64(z).copy()
+    obs = np.ascontiguousarray(obs, dtype=np.uint8).ravel()
+    if step is None:
+        L = lipschitz_codes(cfg, d, int(batch.H.max()), int(batch.W.max()))
+        alpha = 1.0 / L if L > 0 else 0.0
+    else:
+        alpha = float(step)
+    for n in range(batch.n):
+        H, W = int(batch.H[n]), int(batch.W[n])
+        m = mask_image(cfg, t, int(batch.ids[n]), H, W).ravel()
+        zi = np.ascontiguousarray(batch.image(z, n, cfg.K))
+        xi = np.ascontiguousarray(batch.image(x, n))
+        oi = np.ascontiguousarray(batch.image(obs, n))
+        lib().orc_code_update_image_observed(cfg.K, cfg.s, H, W, _p(d), _p(xi), _p(zi), _p(m),
+                                             _p(oi), alpha, cfg.lam, n_iters)
+        o = int(batch.off[n]) * cfg.K
+        z[o:o + zi.size] = zi
+    return z
+
+
 def filter_gradient_batch(cfg: Config, batch: Batch, x, z, d) -> np.ndarray:
     """G = sum_n Z_n^T (D z_n - x_n), the gradient of Eq. 5's objective."""
     x, z, d = _f64(x), _f64(z), _f64(d)

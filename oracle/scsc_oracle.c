@@ -177,6 +177,45 @@ void orc_code_update_image(int K, int s, int H, int W, const double *d,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Inpainting: observed pixels only in the data term (Sec. 4.3)              */
+/* ------------------------------------------------------------------------ */
+
+double orc_objective_image_observed(int K, int s, int H, int W, const double *d,
+                                    const double *z, const double *x, const uint8_t *obs,
+                                    double lambda) {
+  size_t D = (size_t)H * W;
+  double *xh = (double *)malloc(D * sizeof(double));
+  orc_synthesis(K, s, H, W, d, z, xh);
+  double data = 0.0, l1 = 0.0;
+  for (size_t i = 0; i < D; ++i)
+    if (obs[i]) data += (x[i] - xh[i]) * (x[i] - xh[i]);
+  for (size_t i = 0; i < D * (size_t)K; ++i) l1 += fabs(z[i]);
+  free(xh);
+  return 0.5 * data + lambda * l1;
+}
+
+void orc_code_update_image_observed(int K, int s, int H, int W, const double *d,
+                                    const double *x, double *z, const uint8_t *mask,
+                                    const uint8_t *obs, double alpha, double lambda,
+                                    int n_iters) {
+  size_t D = (size_t)H * W, DK = D * (size_t)K;
+  double *r = (double *)malloc(D * sizeof(double));
+  double *g = (double *)malloc(DK * sizeof(double));
+  for (size_t i = 0; i < DK; ++i)
+    if (!mask[i]) z[i] = 0.0;
+  for (int it = 0; it < n_iters; ++it) {
+    orc_synthesis(K, s, H, W, d, z, r);
+    /* gradient of 0.5 || O (x - D z) ||^2 is D^T O (D z - x) */
+    for (size_t i = 0; i < D; ++i) r[i] = obs[i] ? r[i] - x[i] : 0.0;
+    orc_adjoint(K, s, H, W, d, r, g);
+    for (size_t i = 0; i < DK; ++i)
+      if (mask[i]) z[i] = orc_soft_threshold(z[i] - alpha * g[i], alpha * lambda);
+  }
+  free(r);
+  free(g);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Power iterations for the Lipschitz constants of the gradient steps        */
 /* ------------------------------------------------------------------------ */
 

@@ -70,6 +70,19 @@ void orc_code_update_image(int K, int s, int H, int W, const double *d,
                            const double *x, double *z, const uint8_t *mask,
                            double alpha, double lambda, int n_iters);
 
+/* Inpainting (Sec. 4.3, reconstruction from partially observed pixels): the
+ * data term only counts observed pixels, 0.5 || O (x - D z) ||^2 with
+ * O = diag(obs), obs[i] != 0 = observed.
+ *   objective: 0.5 sum_i obs_i (x_i - (D z)_i)^2 + lambda ||z||_1;
+ *   code update: as orc_code_update_image with r = O (D z - x). */
+double orc_objective_image_observed(int K, int s, int H, int W, const double *d,
+                                    const double *z, const double *x, const uint8_t *obs,
+                                    double lambda);
+void orc_code_update_image_observed(int K, int s, int H, int W, const double *d,
+                                    const double *x, double *z, const uint8_t *mask,
+                                    const uint8_t *obs, double alpha, double lambda,
+                                    int n_iters);
+
 /* Power iteration estimate of lambda_max(D D^T) on an H x W pixel domain.
  * Start u_i = +-1 from the top bit of mix(mix(seed ^ tag) ^ i); `iters`
  * normalised applications, then the Rayleigh quotient. */

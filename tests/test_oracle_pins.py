@@ -377,3 +377,61 @@ def test_dense_power_iteration_matches_eigvalsh():
     C = a @ a.T
     est = R.lib().orc_power_dense(30, R._p(np.ascontiguousarray(C)), 1, R.TAG_LC, 200)
     assert est == pytest.approx(np.linalg.eigvalsh(C).max(), rel=1e-9)
+
+
+# ------------------------------------------------------------------ inpainting (observed pixels)
+
+def test_observed_all_ones_equals_the_plain_update_and_objective():
+    K, s, H, W = 3, 5, 12, 15
+    d = I.filters(4, K, s).astype(np.float64)
+    x = I.images(5, [H], [W]).astype(np.float64)
+    z0 = I.sparse_codes(6, H * W, K, density=0.2).astype(np.float64)
+    cfg = R.Config(K=K, s=s, lam=0.3, p_num=2, p_den=3, seed=8)
+    batch = R.Batch(H=[H], W=[W], ids=[2])
+    ones = np.ones(H * W, dtype=np.uint8)
+    za = R.code_step(cfg, batch, x, d, z0, t=2, n_iters=7, step=0.01)
+    zb = R.code_step_observed(cfg, batch, x, d, z0, ones, t=2, n_iters=7, step=0.01)
+    assert np.array_equal(za, zb)
+    assert R.objective(cfg, batch, x, za, d) == R.objective_observed(cfg, batch, x, za, d, ones)
+
+
+def test_observed_none_leaves_pure_shrinkage():
+    """With no observed pixel the gradient vanishes: each PG step only shrinks
+    the sampled codes by alpha * lambda (closed form), and Eq. 4 zeroes the
+    rest."""
+    K, s, H, W = 2, 3, 9, 7
+    d = I.filters(1, K, s).astype(np.float64)
+    x = I.images(2, [H], [W]).astype(np.float64)
+    z0 = rng(4).normal(size=H * W * K)
+    cfg = R.Config(K=K, s=s, lam=0.2, p_num=1, p_den=2, seed=3)
+    batch = R.Batch(H=[H], W=[W], ids=[0])
+    n, alpha = 5, 0.1
+    z = R.code_step_observed(cfg, batch, x, d, z0, np.zeros(H * W, np.uint8), 1, n, step=alpha)
+    m = R.mask_image(cfg, 1, 0, H, W).ravel().astype(bool)
+    want = np.where(m, np.sign(z0) * np.maximum(np.abs(z0) - n * alpha * cfg.lam, 0.0), 0.0)
+    np.testing.assert_allclose(z, want, atol=1e-15)
+    assert R.objective_observed(cfg, batch, x, z, d, np.zeros(H * W, np.uint8)) == \
+        pytest.approx(cfg.lam * np.abs(z).sum(), rel=1e-15)
+
+
+def test_observed_pg_step_matches_explicit_matrices_8x8():
+    """One step z <- soft(z - alpha A^T O (A z - x), alpha lambda) on the
+    sampled set, with the explicit synthesis matrix A and O = diag(obs)."""
+    K, s, H, W = 2, 5, 8, 8
+    d = I.filters(1, K, s).astype(np.float64)
+    x = I.images(2, [H], [W]).astype(np.float64)
+    z0 = rng(11).normal(size=H * W * K) * 0.3
+    obs = (rng(12).random(H * W) < 0.5).astype(np.uint8)
+    cfg = R.Config(K=K, s=s, lam=0.05, p_num=1, p_den=2, seed=21)
+    batch = R.Batch(H=[H], W=[W], ids=[0])
+    alpha = 0.02
+    z1 = R.code_step_observed(cfg, batch, x, d, z0, obs, 1, 1, step=alpha)
+    A = explicit_synthesis_matrix(d, H, W)
+    m = R.mask_image(cfg, 1, 0, H, W).ravel().astype(bool)
+    zm = np.where(m, z0, 0.0)
+    v = zm - alpha * (A.T @ (obs * (A @ zm - x)))
+    want = np.where(m, np.sign(v) * np.maximum(np.abs(v) - alpha * cfg.lam, 0.0), 0.0)
+    np.testing.assert_allclose(z1, want, atol=1e-13)
+    f = R.objective_observed(cfg, batch, x, z1, d, obs)
+    assert f == pytest.approx(0.5 * np.sum(obs * (x - A @ z1) ** 2) + cfg.lam * np.abs(z1).sum(),
+                              rel=1e-13)
