@@ -43,6 +43,11 @@ WORKLOADS = {
                       "(small case for profiler captures)"),
     "c5": dict(n=512, H=None, W=None, K=100, p=(1, 4), n_iters=20,
                desc="512 blob images, H,W uniform in {64..512}, K=100 11x11, p=1/4, 20 PG its/step"),
+    # inpainting (Sec. 4.3): ten 256x256 images, 50% of the pixels observed at
+    # random, lambda = 0.4, 50 iterations, every code coordinate (p = 1)
+    "inpaint": dict(n=10, H=256, W=256, K=100, p=(1, 1), n_iters=50, lam=0.4, observed=0.5,
+                    desc="inpainting: 10 x 256x256 blob images, 50% pixels observed, K=100 11x11, "
+                         "lambda=0.4, p=1, 50 PG its/step"),
 }
 
 
@@ -57,6 +62,14 @@ def make_inputs(wl, rank):
     x = I.images(10 + rank, H, W)
     d = I.filters(7, wl["K"], 11)
     return H, W, ids, x, d
+
+
+def make_observed(wl, rank, H, W):
+    """Observation mask of an inpainting workload (None for the others)."""
+    from paper_1909_00145_gb300 import inputs as I
+    if "observed" not in wl:
+        return None
+    return I.observed_pixels(20 + rank, int(np.dot(H.astype(np.int64), W)), wl["observed"])
 
 
 class ClockSampler:
@@ -158,16 +171,24 @@ def cpu_baseline(wl, budget_s=20.0):
     workload on the host cores (bounded sample)."""
     from oracle import reference as R
     H, W, ids, x, d = make_inputs(dict(wl, n=1), 0)
-    cfg = R.Config(K=wl["K"], s=11, lam=1.0, p_num=wl["p"][0], p_den=wl["p"][1], seed=0)
+    cfg = R.Config(K=wl["K"], s=11, lam=wl.get("lam", 1.0), p_num=wl["p"][0], p_den=wl["p"][1],
+                   seed=0)
     b = R.Batch(H=H[:1], W=W[:1], ids=ids[:1])
     z = np.zeros(int(H[0]) * int(W[0]) * wl["K"])
+    obs = make_observed(dict(wl, n=1), 0, H[:1], W[:1])
     step = 1.0 / 200.0  # fixed step: the sample times the PG iterations only
+
+    def run(n):
+        if obs is None:
+            R.code_step(cfg, b, x, d, z, 1, n, step=step)
+        else:
+            R.code_step_observed(cfg, b, x, d, z, obs, 1, n, step=step)
     t0 = time.perf_counter()
-    R.code_step(cfg, b, x, d, z, 1, 1, step=step)
+    run(1)
     one = time.perf_counter() - t0
     iters = max(1, int(budget_s / max(one, 1e-3)))
     t0 = time.perf_counter()
-    R.code_step(cfg, b, x, d, z, 1, iters, step=step)
+    run(iters)
     el = time.perf_counter() - t0
     pf = int(H[0]) * int(W[0]) * wl["K"] * iters
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
@@ -182,19 +203,26 @@ def run_reference(args, wl):
         return
     from oracle import reference as R
     H, W, ids, x, d = make_inputs(dict(wl, n=1), 0)
-    cfg = R.Config(K=wl["K"], s=11, lam=1.0, p_num=wl["p"][0], p_den=wl["p"][1], seed=0)
+    cfg = R.Config(K=wl["K"], s=11, lam=wl.get("lam", 1.0), p_num=wl["p"][0], p_den=wl["p"][1],
+                   seed=0)
     b = R.Batch(H=H[:1], W=W[:1], ids=ids[:1])
     z = np.zeros(int(H[0]) * int(W[0]) * wl["K"])
+    obs = make_observed(dict(wl, n=1), 0, H[:1], W[:1])
     step = 1.0 / 200.0
+
+    def run(z, n):
+        if obs is None:
+            return R.code_step(cfg, b, x, d, z, 1, n, step=step)
+        return R.code_step_observed(cfg, b, x, d, z, obs, 1, n, step=step)
     t0 = time.perf_counter()
-    R.code_step(cfg, b, x, d, z, 1, 1, step=step)
+    run(z, 1)
     one = time.perf_counter() - t0
     per_step = max(1, int(4.0 / max(one, 1e-3)))
     for i in range(args.warmup):
-        z = R.code_step(cfg, b, x, d, z, 1, per_step, step=step)
+        z = run(z, per_step)
     t0 = time.perf_counter()
     for i in range(args.steps):
-        z = R.code_step(cfg, b, x, d, z, 1, per_step, step=step)
+        z = run(z, per_step)
     el = time.perf_counter() - t0
     pf = int(H[0]) * int(W[0]) * wl["K"] * per_step * args.steps
     val = pf / el / 1e9
@@ -313,7 +341,17 @@ def main():
     flags = (scsc.SCSC_FLAG_PER_IMAGE if args.per_image else 0) | \
         (scsc.SCSC_FLAG_NO_GRAPH if args.no_graph else 0) | \
         (scsc.SCSC_FLAG_NO_AUTOTUNE if args.no_autotune else 0)
-    ctx = scsc.Context(K, 11, 1.0, wl["p"], seed=0, prec=args.prec, stream=stream, flags=flags)
+    lam = wl.get("lam", 1.0)
+    ctx = scsc.Context(K, 11, lam, wl["p"], seed=0, prec=args.prec, stream=stream, flags=flags)
+    obs_np = make_observed(wl, rank, H, W)
+    obs = torch.from_numpy(obs_np).cuda() if obs_np is not None else None
+
+    def code_step(c, x_, d_, z_, t, o=None):
+        """One code step of the workload (inpainting: observed pixels only)."""
+        if obs is None:
+            c.code_step(batch, x_, d_, z_, t, n_iters)
+        else:
+            c.code_step_observed(batch, x_, d_, z_, obs if o is None else o, t, n_iters)
 
     def barrier():
         if world > 1:
@@ -321,7 +359,7 @@ def main():
 
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
-            ctx.code_step(batch, x, d, z, 1 + i, n_iters)
+            code_step(ctx, x, d, z, 1 + i)
         ctx.sync()
         z_warm = z.clone()
         sampler = ClockSampler(local)
@@ -332,7 +370,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(args.steps):
-            ctx.code_step(batch, x, d, z, 100 + i, n_iters)
+            code_step(ctx, x, d, z, 100 + i)
         e1.record(stream)
         torch.cuda.synchronize()
         clocks = sampler.stop()
@@ -354,7 +392,7 @@ def main():
     with torch.cuda.stream(stream):
         scsc.scsc_diag_profile(ctx, True)
         for i in range(prof_steps):
-            ctx.code_step(batch, x, d, z, 100 + i, n_iters)
+            code_step(ctx, x, d, z, 100 + i)
         ctx.sync()
         for name in ["synth_tc", "adj_tc", "finalize_r", "synth_fp32", "adjoint_fp32", "pack",
                      "unpack", "power", "mask"]:
@@ -368,12 +406,16 @@ def main():
     rel_err = None
     if args.prec != "fp32":
         with torch.cuda.stream(stream):
-            ref = scsc.Context(K, 11, 1.0, wl["p"], seed=0, prec="fp32", stream=stream)
+            ref = scsc.Context(K, 11, lam, wl["p"], seed=0, prec="fp32", stream=stream)
             za, zb = z_warm.clone(), z_warm.clone()
-            ctx.code_step(batch, x, d, za, 500, n_iters)
-            ref.code_step(batch, x, d, zb, 500, n_iters)
-            fa = ctx.objective(batch, x, za, d)
-            fb = ref.objective(batch, x, zb, d)
+            code_step(ctx, x, d, za, 500)
+            code_step(ref, x, d, zb, 500)
+            if obs is None:
+                fa = ctx.objective(batch, x, za, d)
+                fb = ref.objective(batch, x, zb, d)
+            else:
+                fa = ctx.objective_observed(batch, x, za, d, obs)
+                fb = ref.objective_observed(batch, x, zb, d, obs)
             rel_err = abs(fa - fb) / abs(fb)
             ref.close()
             del za, zb
@@ -407,8 +449,10 @@ def main():
     xh = torch.from_numpy(x_np).pin_memory()
     dh = torch.from_numpy(d_np).contiguous().pin_memory()
     zh = torch.zeros(npx * K, dtype=torch.float32).pin_memory()
+    oh = torch.from_numpy(obs_np).pin_memory() if obs is not None else None
     with torch.cuda.stream(stream):
         xd, dd, zd = torch.empty_like(x), torch.empty_like(d), torch.empty_like(z)
+        od = torch.empty_like(obs) if obs is not None else None
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
@@ -416,7 +460,9 @@ def main():
             xd.copy_(xh, non_blocking=True)
             dd.copy_(dh, non_blocking=True)
             zd.copy_(zh, non_blocking=True)
-            ctx.code_step(batch, xd, dd, zd, 200 + i, n_iters)
+            if od is not None:
+                od.copy_(oh, non_blocking=True)
+            code_step(ctx, xd, dd, zd, 200 + i, od)
             zh.copy_(zd, non_blocking=True)
             stream.synchronize()
         e2e_s = time.perf_counter() - t0
@@ -425,7 +471,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_val = npx * K * n_iters * args.e2e_steps * world / e2e_s / 1e9
-    h2d = x.numel() * 4 + d.numel() * 4 + z.numel() * 4
+    h2d = x.numel() * 4 + d.numel() * 4 + z.numel() * 4 + (obs.numel() if obs is not None else 0)
     d2h = z.numel() * 4
 
     if rank == 0:
@@ -435,7 +481,8 @@ def main():
                "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
                "config": {"workload": wl["desc"], "images_per_gpu": int(len(H)),
                           "pixels_per_gpu": npx, "K": K, "p": f"{wl['p'][0]}/{wl['p'][1]}",
-                          "n_iters": n_iters, "path": args.prec,
+                          "n_iters": n_iters, "lambda": lam, "path": args.prec,
+                          **({"observed_fraction": wl["observed"]} if "observed" in wl else {}),
                           "launches": "per image" if args.per_image else "batched",
                           "graph": not args.no_graph,
                           "l2": "inputs larger than L2 (dense codes %.2f GB)" % (npx * K * 4 / 1e9)},

@@ -117,6 +117,18 @@ scsc_status scsc_mask(scsc_ctx *ctx, const scsc_batch *batch, uint64_t t, uint32
 scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
                            const float *d_dev, float *z_dev, uint64_t t, int n_iters);
 
+/* Inpainting (Sec. 4.3: reconstruction from partially observed pixels): the
+ * code update of scsc_code_step with the data term counted on observed pixels
+ * only, 1/2 || O (x - D (M^t)^T z~) ||^2, O = diag(observed), so the residual
+ * is r = O (D z - x).  observed_dev: device, one byte per pixel of the batch
+ * (x's layout), nonzero = observed; the caller keeps it alive until the call's
+ * work on the stream has run.  NULL observed_dev = every pixel observed
+ * (exactly scsc_code_step).  The step size is scsc_code_step's 1 / L_z, a
+ * valid step because ||O D|| <= ||D||.  Errors as scsc_code_step. */
+scsc_status scsc_code_step_observed(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                                    const float *d_dev, float *z_dev,
+                                    const uint8_t *observed_dev, uint64_t t, int n_iters);
+
 /* Dictionary update.  SCSC_DICT_BATCH (Eq. 5): r = D z - x,
  * G_k(u,v) = sum_n sum_{i,j} r(i,j) z_k(i+c-u, j+c-v),
  * d_k <- P(d_k - G_k / L_d) with L_d from the power-iteration rule on
@@ -129,6 +141,13 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
 /* Eq. 1 summed over the batch, accumulated in FP64; synchronises. */
 scsc_status scsc_objective(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
                            const float *z_dev, const float *d_dev, double *out_host);
+
+/* Objective of the inpainting problem: 1/2 sum over observed pixels of
+ * (x - D z)^2 + lambda ||z||_1, summed over the batch in FP64; observed_dev
+ * as in scsc_code_step_observed (NULL = scsc_objective); synchronises. */
+scsc_status scsc_objective_observed(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                                    const float *z_dev, const float *d_dev,
+                                    const uint8_t *observed_dev, double *out_host);
 
 /* L_z = 1.01 x power-iteration estimate of lambda_max(D D^T) on the batch's
  * max(H) x max(W) domain (the step-size rule of scsc_code_step); synchronises. */

@@ -65,6 +65,13 @@ __global__ void __launch_bounds__(256) mask_bits_kernel(BatchDev b, int K, int K
   }
 }
 
+// r <- O r: zero the residual at unobserved pixels (inpainting data term).
+__global__ void mask_residual_kernel(float *r, const uint8_t *obs, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (obs[i] == 0) r[i] = 0.0f;
+}
+
 __global__ void apply_mask_dense_kernel(int64_t total, int K, int KW, const uint32_t *bits,
                                         float *z) {
   for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
@@ -522,6 +529,12 @@ cudaError_t launch_mask_bits(const BatchDev &b, int K, uint64_t seed, uint64_t t
   int KW = (K + 31) / 32;
   if (b.total_px == 0 || b.n_tiles == 0) return cudaSuccess;
   mask_bits_kernel<<<b.n_tiles, 256, 0, st>>>(b, K, KW, seed, t, T, bits);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_residual(float *r, const uint8_t *obs, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  mask_residual_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, st>>>(r, obs, n);
   return cudaGetLastError();
 }
 

@@ -366,6 +366,7 @@ __global__ void __launch_bounds__(kThreads) finalize_r_kernel(ItemMap im, int C,
                                                               const float *__restrict__ xcore,
                                                               const float *__restrict__ spill,
                                                               const float *__restrict__ x,
+                                                              const uint8_t *__restrict__ obs,
                                                               float *__restrict__ r) {
   const int q_begin = (int)((int64_t)im.total * blockIdx.x / gridDim.x);
   const int q_end = (int)((int64_t)im.total * (blockIdx.x + 1) / gridDim.x);
@@ -389,7 +390,8 @@ __global__ void __launch_bounds__(kThreads) finalize_r_kernel(ItemMap im, int C,
       if (lc >= kStrip - C && it.js + 1 < it.JS)
         v += spill[(int64_t)(q + it.H) * (2 * C) + lc - (kStrip - C)];
     }
-    r[p] = v - x[p];
+    // inpainting: the data term counts observed pixels only
+    r[p] = (obs != nullptr && obs[p] == 0) ? 0.0f : v - x[p];
   }
 }
 
@@ -682,8 +684,8 @@ void tc_release(TcWorkspace &ws) {
 
 cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, const int *W_host,
                          int K, int s, const float *x, const float *d, float *z,
-                         const uint32_t *bits, const StepParams *prm, int n_iters,
-                         cudaStream_t st) {
+                         const uint32_t *bits, const uint8_t *obs, const StepParams *prm,
+                         int n_iters, cudaStream_t st) {
   if (K > 256) {
     ws.last_error = "the tensor path supports K <= 256";
     return cudaErrorNotSupported;
@@ -807,7 +809,7 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
     if (ws.prof) ws.prof->end(p1, st);
     int p2 = ws.prof ? ws.prof->begin(KID_FINALIZE, st) : -1;
     finalize_r_kernel<<<fin_grid, kThreads, 0, st>>>(im, C, as<float>(ws.xcore), as<float>(ws.spill),
-                                                      x, as<float>(ws.r));
+                                                      x, obs, as<float>(ws.r));
     TRY(cudaGetLastError());
     if (ws.prof) ws.prof->end(p2, st);
     int p3 = ws.prof ? ws.prof->begin(KID_ADJ_TC, st) : -1;
@@ -874,8 +876,8 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
                          !(ws.prof && ws.prof->on);
   if (use_graph) {
     const GraphKey gk{bits, seg_base, pxoff, ws.packed.p, ws.bsyn.p, ws.badj.p, ws.xcore.p,
-                      ws.spill.p, ws.r.p, ws.err.p, x, prm, ws.item0.p, b.off, K, s, Q,
-                      variant, rem};
+                      ws.spill.p, ws.r.p, ws.err.p, x, prm, ws.item0.p, b.off, obs, K, s,
+                      Q, variant, rem};
     if (!ws.graph_exec || std::memcmp(&gk, &ws.graph_key, sizeof gk) != 0) {
       if (ws.graph_exec) cudaGraphExecDestroy(ws.graph_exec);
       ws.graph_exec = nullptr;

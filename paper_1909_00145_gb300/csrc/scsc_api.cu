@@ -403,8 +403,10 @@ scsc_status scsc_lipschitz_codes(scsc_ctx *ctx, const scsc_batch *batch, const f
   return SCSC_OK;
 }
 
-scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
-                           const float *d_dev, float *z_dev, uint64_t t, int n_iters) {
+// scsc_code_step / scsc_code_step_observed (obs = NULL: every pixel observed).
+static scsc_status code_step_impl(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                           const float *d_dev, float *z_dev, const uint8_t *obs, uint64_t t,
+                           int n_iters) {
   if (!ctx) return SCSC_EINVAL;
   if (!x_dev || !d_dev || !z_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
   if (n_iters < 0) return fail(ctx, SCSC_EINVAL, "n_iters = %d < 0", n_iters);
@@ -420,7 +422,7 @@ scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
     if (!errw) return fail(ctx, SCSC_ENOMEM, "tensor path: error word allocation failed");
     CK(cudaMemsetAsync(errw, 0, sizeof(int), st));
     cudaError_t e = tc_code_step(ctx->tc, b, batch->H, batch->W, K, s, x_dev, d_dev, z_dev,
-                                 ctx->bits.as<uint32_t>(), prm, n_iters, st);
+                                 ctx->bits.as<uint32_t>(), obs, prm, n_iters, st);
     if (e == cudaErrorNotSupported)
       return fail(ctx, SCSC_EUNSUPPORTED, "tensor path: %s", tc_last_error(ctx->tc));
     if (e == cudaErrorTimeout)
@@ -445,6 +447,7 @@ scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
       CK(launch_synth_fp32(v, K, s, d_dev, z_dev, nullptr, x_dev, ctx->r.as<float>(), st));
       ctx->prof.end(p1, st);
     }
+    if (obs) CK(launch_mask_residual(ctx->r.as<float>(), obs, b.total_px, st));
     for (const BatchDev &v : views) {
       int p2 = ctx->prof.begin(KID_ADJ_FP32, st);
       CK(launch_adjoint_fp32(v, K, s, d_dev, ctx->r.as<float>(), ctx->bits.as<uint32_t>(), 1,
@@ -455,8 +458,9 @@ scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
   return SCSC_OK;
 }
 
-scsc_status scsc_objective(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
-                           const float *z_dev, const float *d_dev, double *out_host) {
+static scsc_status objective_impl(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                           const float *z_dev, const float *d_dev, const uint8_t *obs,
+                           double *out_host) {
   if (!ctx) return SCSC_EINVAL;
   if (!x_dev || !z_dev || !d_dev || !out_host) return fail(ctx, SCSC_EINVAL, "NULL pointer");
   CKS(stage_batch(ctx, batch));
@@ -467,6 +471,7 @@ scsc_status scsc_objective(scsc_ctx *ctx, const scsc_batch *batch, const float *
   CK(ctx->scal.ensure(8 * 8));
   CK(launch_synth_fp32(b, ctx->cfg.K, ctx->cfg.s, d_dev, z_dev, nullptr, x_dev, ctx->r.as<float>(),
                        st));
+  if (obs) CK(launch_mask_residual(ctx->r.as<float>(), obs, b.total_px, st));
   CK(launch_sum_sq_abs(ctx->r.as<float>(), b.total_px, z_dev, b.total_px * ctx->cfg.K,
                        ctx->partials.as<double>(), kRedBlocks, st));
   CK(launch_finish_sum(ctx->partials.as<double>(), kRedBlocks, 0.5, ctx->cfg.lambda,
@@ -474,6 +479,28 @@ scsc_status scsc_objective(scsc_ctx *ctx, const scsc_batch *batch, const float *
   CK(cudaMemcpyAsync(out_host, ctx->scal.as<double>() + 4, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return SCSC_OK;
+}
+
+scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                           const float *d_dev, float *z_dev, uint64_t t, int n_iters) {
+  return code_step_impl(ctx, batch, x_dev, d_dev, z_dev, nullptr, t, n_iters);
+}
+
+scsc_status scsc_code_step_observed(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                                    const float *d_dev, float *z_dev,
+                                    const uint8_t *observed_dev, uint64_t t, int n_iters) {
+  return code_step_impl(ctx, batch, x_dev, d_dev, z_dev, observed_dev, t, n_iters);
+}
+
+scsc_status scsc_objective(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                           const float *z_dev, const float *d_dev, double *out_host) {
+  return objective_impl(ctx, batch, x_dev, z_dev, d_dev, nullptr, out_host);
+}
+
+scsc_status scsc_objective_observed(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                                    const float *z_dev, const float *d_dev,
+                                    const uint8_t *observed_dev, double *out_host) {
+  return objective_impl(ctx, batch, x_dev, z_dev, d_dev, observed_dev, out_host);
 }
 
 scsc_status scsc_synth(scsc_ctx *ctx, const scsc_batch *batch, const float *z_dev,

@@ -91,6 +91,8 @@ cudaError_t launch_sum_sq_abs(const float *a, int64_t n_sq, const float *b, int6
                               double *partials, int n_blocks, cudaStream_t st);
 cudaError_t launch_finish_sum(const double *partials, int n_blocks, double scale_sq,
                               double scale_abs, double *out, cudaStream_t st);
+// r[i] = 0 where obs[i] == 0 (observed-pixel data term).
+cudaError_t launch_mask_residual(float *r, const uint8_t *obs, int64_t n, cudaStream_t st);
 // D D^T of the step-size domain as per-class stencils (kernels_ddt.cu):
 // prepare builds the tap Gram matrix G (FP64, (s*s)^2) and the stencils A
 // (ddt_stencil_floats(s, H, W) floats) from d; apply computes w = D D^T u.

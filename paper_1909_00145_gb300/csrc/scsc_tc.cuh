@@ -23,7 +23,7 @@ struct TuneKey {
 // Everything a captured iteration graph depends on.
 struct GraphKey {
   const void *bits, *seg_base, *pxoff, *packed, *bsyn, *badj, *xcore, *spill, *r, *err, *x, *prm,
-      *item0, *off;
+      *item0, *off, *obs;
   int K, s, Q, variant, iters;
 };
 
@@ -53,10 +53,12 @@ struct TcWorkspace {
 // proximal-gradient iterations on packed FP32 codes with BF16 tcgen05
 // synthesis and adjoint, unpack to dense codes (Eq. 4).
 // H_host / W_host are the batch's host arrays (n images).
+// obs: one byte per pixel, nonzero = observed (data term on observed pixels
+// only); NULL = every pixel observed.
 cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, const int *W_host,
                          int K, int s, const float *x, const float *d, float *z,
-                         const uint32_t *bits, const StepParams *prm, int n_iters,
-                         cudaStream_t st);
+                         const uint32_t *bits, const uint8_t *obs, const StepParams *prm,
+                         int n_iters, cudaStream_t st);
 // Device error word of the tensor kernels (0 = ok, 1 = bounded wait ran out).
 int *tc_error_word(TcWorkspace &ws);
 void tc_release(TcWorkspace &ws);

@@ -64,3 +64,10 @@ def uneven_sizes(seed: int, n_images: int, lo: int = 64, hi: int = 512):
     H = rng.integers(lo, hi + 1, n_images)
     W = rng.integers(lo, hi + 1, n_images)
     return H.astype(np.int32), W.astype(np.int32)
+
+
+def observed_pixels(seed: int, n_pixels: int, fraction: float = 0.5) -> np.ndarray:
+    """Inpainting observation mask: each pixel observed (1) independently with
+    the given probability (the paper's experiment observes 50% at random)."""
+    rng = np.random.default_rng(seed)
+    return (rng.random(n_pixels) < fraction).astype(np.uint8)

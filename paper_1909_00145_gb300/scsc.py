@@ -57,8 +57,12 @@ _SIGNATURES = {
     "scsc_mask": [c_void_p, ctypes.POINTER(scsc_batch), c_u64, c_void_p],
     "scsc_code_step": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p, c_u64,
                        c_int],
+    "scsc_code_step_observed": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p,
+                                c_void_p, c_void_p, c_u64, c_int],
     "scsc_dict_step": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p, c_int,
                        c_u64],
+    "scsc_objective_observed": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p,
+                                c_void_p, c_void_p, ctypes.POINTER(c_double)],
     "scsc_objective": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p,
                        ctypes.POINTER(c_double)],
     "scsc_lipschitz_codes": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p,
@@ -185,6 +189,12 @@ class Context:
     def code_step(self, batch, x, d, z, t, n_iters):
         return scsc_code_step(self, batch, x, d, z, t, n_iters)
 
+    def code_step_observed(self, batch, x, d, z, observed, t, n_iters):
+        return scsc_code_step_observed(self, batch, x, d, z, observed, t, n_iters)
+
+    def objective_observed(self, batch, x, z, d, observed) -> float:
+        return scsc_objective_observed(self, batch, x, z, d, observed)
+
     def dict_step(self, batch, x, z, d, mode=SCSC_DICT_BATCH, t=1):
         return scsc_dict_step(self, batch, x, z, d, mode, t)
 
@@ -245,6 +255,24 @@ def scsc_objective(ctx: Context, batch: Batch, x, z, d) -> float:
     out = c_double()
     _check(lib().scsc_objective(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(z), _ptr(d),
                                 ctypes.byref(out)), ctx.handle, "scsc_objective")
+    return out.value
+
+
+def scsc_code_step_observed(ctx: Context, batch: Batch, x, d, z, observed, t: int,
+                            n_iters: int) -> None:
+    """Inpainting code update: observed is a uint8 device tensor, one byte per
+    pixel (nonzero = observed), or None for every pixel."""
+    _check(lib().scsc_code_step_observed(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d),
+                                         _ptr(z), _ptr(observed) if observed is not None else None,
+                                         t, n_iters), ctx.handle, "scsc_code_step_observed")
+
+
+def scsc_objective_observed(ctx: Context, batch: Batch, x, z, d, observed) -> float:
+    out = c_double()
+    _check(lib().scsc_objective_observed(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(z),
+                                         _ptr(d),
+                                         _ptr(observed) if observed is not None else None,
+                                         ctypes.byref(out)), ctx.handle, "scsc_objective_observed")
     return out.value
 
 
