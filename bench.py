@@ -48,6 +48,11 @@ WORKLOADS = {
     "inpaint": dict(n=10, H=256, W=256, K=100, p=(1, 1), n_iters=50, lam=0.4, observed=0.5,
                     desc="inpainting: 10 x 256x256 blob images, 50% pixels observed, K=100 11x11, "
                          "lambda=0.4, p=1, 50 PG its/step"),
+    # the paper's ADMM code solver (Sec. 3.2) on its fruit-set shape: ten
+    # 100x100 images, K=100, p=0.1, 10 ADMM iterations (20 CG steps each)
+    "admm": dict(n=10, H=100, W=100, K=100, p=(1, 10), n_iters=10, solver="admm", cg_iters=20,
+                 desc="ADMM code step: 10 x 100x100 blob images, K=100 11x11, p=1/10, lambda=1, "
+                      "10 ADMM its x 20 CG steps/step (plain FP32 operators)"),
 }
 
 
@@ -347,8 +352,11 @@ def main():
     obs = torch.from_numpy(obs_np).cuda() if obs_np is not None else None
 
     def code_step(c, x_, d_, z_, t, o=None):
-        """One code step of the workload (inpainting: observed pixels only)."""
-        if obs is None:
+        """One code step of the workload (inpainting: observed pixels only;
+        the ADMM workload: the ADMM solver)."""
+        if wl.get("solver") == "admm":
+            c.code_step_admm(batch, x_, d_, z_, t, n_iters, wl["cg_iters"])
+        elif obs is None:
             c.code_step(batch, x_, d_, z_, t, n_iters)
         else:
             c.code_step_observed(batch, x_, d_, z_, obs if o is None else o, t, n_iters)

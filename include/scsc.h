@@ -129,6 +129,23 @@ scsc_status scsc_code_step_observed(scsc_ctx *ctx, const scsc_batch *batch, cons
                                     const float *d_dev, float *z_dev,
                                     const uint8_t *observed_dev, uint64_t t, int n_iters);
 
+/* The paper's own solver for Eq. 3 (Sec. 3.2): ADMM on
+ *   min 1/2 || x - D (M^t)^T z~ ||^2 + lambda || y ||_1  s.t.  z~ = y,
+ * per image, n_iters times:
+ *   z~ <- solution of (A^T A + rho I) z~ = A^T x + rho (y - u), A = D (M^t)^T,
+ *         by cg_iters conjugate-gradient steps from the current z~ (stopped
+ *         early once the squared residual is below 1e-30 max(||b||^2, 1));
+ *   zh = alpha z~ + (1 - alpha) y  (over-relaxation);
+ *   y <- soft(zh + u, lambda / rho);  u <- u + zh - y.
+ * z_dev in: warm start (its sampled coordinates start z~ and y; u = 0);
+ * out: y on the sampled set, zero elsewhere (Eq. 4).  rho <= 0 selects the
+ * paper's 10 lambda, alpha <= 0 its 1.8 (alpha must be < 2).  Plain FP32
+ * operators, FP64 CG reductions, for every precision setting.  Errors as
+ * scsc_code_step; SCSC_EINVAL for n_iters or cg_iters < 0. */
+scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                                const float *d_dev, float *z_dev, uint64_t t, int n_iters,
+                                int cg_iters, double rho, double alpha);
+
 /* Dictionary update.  SCSC_DICT_BATCH (Eq. 5): r = D z - x,
  * G_k(u,v) = sum_n sum_{i,j} r(i,j) z_k(i+c-u, j+c-v),
  * d_k <- P(d_k - G_k / L_d) with L_d from the power-iteration rule on

@@ -74,6 +74,7 @@ struct scsc_ctx {
   int domainH = -1, domainW = -1;
   DevBuf bits, r, pix2, prm, scal, partials, gpart, gsum, pu, pw, flag;
   DevBuf ddtG, ddtA;  // tap Gram matrix and per-class stencils of D D^T
+  DevBuf admm;        // ADMM vectors: y, u, b, A^T x, CG residual, direction, QP image
   // tensor path
   TcWorkspace tc;
   // online surrogates
@@ -363,7 +364,7 @@ scsc_status scsc_destroy(scsc_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (DevBuf *b : {&ctx->bits, &ctx->r, &ctx->pix2, &ctx->prm, &ctx->scal, &ctx->partials,
                     &ctx->gpart, &ctx->gsum, &ctx->pu, &ctx->pw,
-                    &ctx->flag, &ctx->ddtG, &ctx->ddtA,
+                    &ctx->flag, &ctx->ddtG, &ctx->ddtA, &ctx->admm,
                     &ctx->C, &ctx->B, &ctx->Cd, &ctx->batch.dev, &ctx->domain.dev})
     b->release();
   for (BatchCache *bc : {&ctx->batch, &ctx->domain}) {
@@ -495,6 +496,75 @@ scsc_status scsc_code_step_observed(scsc_ctx *ctx, const scsc_batch *batch, cons
 scsc_status scsc_objective(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
                            const float *z_dev, const float *d_dev, double *out_host) {
   return objective_impl(ctx, batch, x_dev, z_dev, d_dev, nullptr, out_host);
+}
+
+scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                                const float *d_dev, float *z_dev, uint64_t t, int n_iters,
+                                int cg_iters, double rho, double alpha_r) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!x_dev || !d_dev || !z_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
+  if (n_iters < 0 || cg_iters < 0)
+    return fail(ctx, SCSC_EINVAL, "n_iters = %d, cg_iters = %d must be >= 0", n_iters, cg_iters);
+  if (rho <= 0.0) rho = 10.0 * ctx->cfg.lambda;
+  if (alpha_r <= 0.0) alpha_r = 1.8;
+  if (!std::isfinite(rho) || !std::isfinite(alpha_r) || alpha_r >= 2.0)
+    return fail(ctx, SCSC_EINVAL, "rho = %g, alpha = %g outside rho > 0, 0 < alpha < 2", rho,
+                alpha_r);
+  CKS(stage_batch(ctx, batch));
+  CKS(build_mask(ctx, t));
+  const BatchCache &bc = ctx->batch;
+  const BatchDev &b = bc.view;
+  const int K = ctx->cfg.K, s = ctx->cfg.s, KW = KW_of(ctx);
+  cudaStream_t st = ctx->stream;
+  const int64_t DK = b.total_px * K;
+  CK(ctx->admm.ensure((size_t)7 * DK * 4));
+  CK(ctx->r.ensure((size_t)b.total_px * 4));
+  CK(ctx->partials.ensure((size_t)4 * kRedBlocks * 8));
+  float *const base = ctx->admm.as<float>();
+  float *const y = base, *const u = base + DK, *const bv = base + 2 * DK, *const atx = base + 3 * DK,
+              *const res = base + 4 * DK, *const pv = base + 5 * DK, *const Ap = base + 6 * DK;
+  double *rr = ctx->partials.as<double>(), *rr2 = rr + kRedBlocks, *pap = rr + 2 * kRedBlocks,
+         *bb = rr + 3 * kRedBlocks;
+  float *const pix = ctx->r.as<float>();
+  const uint32_t *bits = ctx->bits.as<uint32_t>();
+  const float frho = (float)rho;
+  const int64_t *off = reinterpret_cast<const int64_t *>(bc.host.data());
+  // One image at a time: the CG scalars are per image, as in the per-image
+  // solver of the paper.  Vectors use the batch's code layout.
+  for (int i = 0; i < b.n; ++i) {
+    const BatchDev v = image_view(bc, i);
+    const int64_t o = off[i] * K, n = v.total_px * K;
+    const uint32_t *bi = bits + off[i] * KW;
+    float *zi = z_dev + o;
+    // QP operator: out = m (D^T D (m in)) + rho m in
+    auto apply_qp = [&](const float *in_global, float *out_global) -> scsc_status {
+      CK(launch_synth_fp32(v, K, s, d_dev, in_global, bits, nullptr, pix, st));
+      CK(launch_adjoint_fp32(v, K, s, d_dev, pix, bits, 0, nullptr, out_global, st));
+      CK(launch_admm_qp_finish(in_global + o, out_global + o, bi, K, frho, n, st));
+      return SCSC_OK;
+    };
+    CK(launch_admm_init(zi, y + o, u + o, bi, K, n, st));
+    CK(launch_adjoint_fp32(v, K, s, d_dev, x_dev, nullptr, 0, nullptr, atx, st));
+    for (int it = 0; it < n_iters; ++it) {
+      CK(launch_admm_rhs(atx + o, y + o, u + o, bv + o, bi, K, frho, n, st));
+      CKS(apply_qp(z_dev, Ap));
+      CK(launch_cg_init(bv + o, Ap + o, res + o, pv + o, n, st));
+      CK(launch_dot_partials(res + o, res + o, n, rr, kRedBlocks, st));
+      CK(launch_dot_partials(bv + o, bv + o, n, bb, kRedBlocks, st));
+      for (int k = 0; k < cg_iters; ++k) {
+        CKS(apply_qp(pv, Ap));
+        CK(launch_dot_partials(pv + o, Ap + o, n, pap, kRedBlocks, st));
+        CK(launch_cg_step(zi, res + o, pv + o, Ap + o, rr, pap, bb, kRedBlocks, n, st));
+        CK(launch_dot_partials(res + o, res + o, n, rr2, kRedBlocks, st));
+        CK(launch_cg_direction(pv + o, res + o, rr2, rr, bb, kRedBlocks, n, st));
+        std::swap(rr, rr2);
+      }
+      CK(launch_admm_shrink(zi, y + o, u + o, bi, K, (float)alpha_r,
+                            (float)(ctx->cfg.lambda / rho), n, st));
+    }
+    CK(launch_admm_final(zi, y + o, bi, K, n, st));
+  }
+  return SCSC_OK;
 }
 
 scsc_status scsc_objective_observed(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,

@@ -59,6 +59,8 @@ _SIGNATURES = {
                        c_int],
     "scsc_code_step_observed": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_u64, c_int],
+    "scsc_code_step_admm": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p,
+                            c_u64, c_int, c_int, c_double, c_double],
     "scsc_dict_step": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p, c_int,
                        c_u64],
     "scsc_objective_observed": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p,
@@ -192,6 +194,9 @@ class Context:
     def code_step_observed(self, batch, x, d, z, observed, t, n_iters):
         return scsc_code_step_observed(self, batch, x, d, z, observed, t, n_iters)
 
+    def code_step_admm(self, batch, x, d, z, t, n_iters, cg_iters, rho=0.0, alpha=0.0):
+        return scsc_code_step_admm(self, batch, x, d, z, t, n_iters, cg_iters, rho, alpha)
+
     def objective_observed(self, batch, x, z, d, observed) -> float:
         return scsc_objective_observed(self, batch, x, z, d, observed)
 
@@ -265,6 +270,14 @@ def scsc_code_step_observed(ctx: Context, batch: Batch, x, d, z, observed, t: in
     _check(lib().scsc_code_step_observed(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d),
                                          _ptr(z), _ptr(observed) if observed is not None else None,
                                          t, n_iters), ctx.handle, "scsc_code_step_observed")
+
+
+def scsc_code_step_admm(ctx: Context, batch: Batch, x, d, z, t: int, n_iters: int,
+                        cg_iters: int, rho: float = 0.0, alpha: float = 0.0) -> None:
+    """ADMM code update (rho, alpha <= 0: the paper's 10 lambda and 1.8)."""
+    _check(lib().scsc_code_step_admm(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d), _ptr(z),
+                                     t, n_iters, cg_iters, float(rho), float(alpha)), ctx.handle,
+           "scsc_code_step_admm")
 
 
 def scsc_objective_observed(ctx: Context, batch: Batch, x, z, d, observed) -> float:
