@@ -184,7 +184,10 @@ def cpu_baseline(wl, budget_s=20.0):
     step = 1.0 / 200.0  # fixed step: the sample times the PG iterations only
 
     def run(n):
-        if obs is None:
+        if wl.get("solver") == "admm":
+            m = R.mask_image(cfg, 1, int(ids[0]), int(H[0]), int(W[0])).ravel()
+            R.admm_image(cfg, d, x, z, m, int(H[0]), int(W[0]), n, cg_iters=wl["cg_iters"])
+        elif obs is None:
             R.code_step(cfg, b, x, d, z, 1, n, step=step)
         else:
             R.code_step_observed(cfg, b, x, d, z, obs, 1, n, step=step)
@@ -197,9 +200,11 @@ def cpu_baseline(wl, budget_s=20.0):
     el = time.perf_counter() - t0
     pf = int(H[0]) * int(W[0]) * wl["K"] * iters
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    what = (f"{iters} ADMM iterations x {wl['cg_iters']} CG steps" if wl.get("solver") == "admm"
+            else f"{iters} PG iterations")
     return {"value": pf / el / 1e9, "unit": "Gpix*filter/s", "cores": cores, "kind": "oracle",
             "sample": f"1 image {int(H[0])}x{int(W[0])} of the workload, K={wl['K']}, "
-                      f"{iters} PG iterations (FP64, dense adjoint, OpenMP), {el:.1f} s"}
+                      f"{what} (FP64, dense adjoint, OpenMP), {el:.1f} s"}
 
 
 def run_reference(args, wl):
@@ -216,6 +221,10 @@ def run_reference(args, wl):
     step = 1.0 / 200.0
 
     def run(z, n):
+        if wl.get("solver") == "admm":
+            m = R.mask_image(cfg, 1, int(ids[0]), int(H[0]), int(W[0])).ravel()
+            return R.admm_image(cfg, d, x, z, m, int(H[0]), int(W[0]), n,
+                                cg_iters=wl["cg_iters"])
         if obs is None:
             return R.code_step(cfg, b, x, d, z, 1, n, step=step)
         return R.code_step_observed(cfg, b, x, d, z, obs, 1, n, step=step)

@@ -131,7 +131,8 @@ scsc_status scsc_code_step_observed(scsc_ctx *ctx, const scsc_batch *batch, cons
 
 /* The paper's own solver for Eq. 3 (Sec. 3.2): ADMM on
  *   min 1/2 || x - D (M^t)^T z~ ||^2 + lambda || y ||_1  s.t.  z~ = y,
- * per image, n_iters times:
+ * each image with its own CG scalars (the whole batch per launch), n_iters
+ * times:
  *   z~ <- solution of (A^T A + rho I) z~ = A^T x + rho (y - u), A = D (M^t)^T,
  *         by cg_iters conjugate-gradient steps from the current z~ (stopped
  *         early once the squared residual is below 1e-30 max(||b||^2, 1));

@@ -75,6 +75,7 @@ struct scsc_ctx {
   DevBuf bits, r, pix2, prm, scal, partials, gpart, gsum, pu, pw, flag;
   DevBuf ddtG, ddtA;  // tap Gram matrix and per-class stencils of D D^T
   DevBuf admm;        // ADMM vectors: y, u, b, A^T x, CG residual, direction, QP image
+  DevBuf admm_partials;  // per-image FP64 partials of the CG dot products
   // tensor path
   TcWorkspace tc;
   // online surrogates
@@ -364,7 +365,7 @@ scsc_status scsc_destroy(scsc_ctx *ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (DevBuf *b : {&ctx->bits, &ctx->r, &ctx->pix2, &ctx->prm, &ctx->scal, &ctx->partials,
                     &ctx->gpart, &ctx->gsum, &ctx->pu, &ctx->pw,
-                    &ctx->flag, &ctx->ddtG, &ctx->ddtA, &ctx->admm,
+                    &ctx->flag, &ctx->ddtG, &ctx->ddtA, &ctx->admm, &ctx->admm_partials,
                     &ctx->C, &ctx->B, &ctx->Cd, &ctx->batch.dev, &ctx->domain.dev})
     b->release();
   for (BatchCache *bc : {&ctx->batch, &ctx->domain}) {
@@ -512,58 +513,55 @@ scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const fl
                 alpha_r);
   CKS(stage_batch(ctx, batch));
   CKS(build_mask(ctx, t));
-  const BatchCache &bc = ctx->batch;
-  const BatchDev &b = bc.view;
-  const int K = ctx->cfg.K, s = ctx->cfg.s, KW = KW_of(ctx);
+  const BatchDev &b = ctx->batch.view;
+  const int K = ctx->cfg.K, s = ctx->cfg.s;
   cudaStream_t st = ctx->stream;
   const int64_t DK = b.total_px * K;
+  const size_t np = (size_t)b.n * kAdmmBlocks;  // partials per dot product
   CK(ctx->admm.ensure((size_t)7 * DK * 4));
   CK(ctx->r.ensure((size_t)b.total_px * 4));
-  CK(ctx->partials.ensure((size_t)4 * kRedBlocks * 8));
+  CK(ctx->admm_partials.ensure(4 * np * 8));
   float *const base = ctx->admm.as<float>();
   float *const y = base, *const u = base + DK, *const bv = base + 2 * DK, *const atx = base + 3 * DK,
               *const res = base + 4 * DK, *const pv = base + 5 * DK, *const Ap = base + 6 * DK;
-  double *rr = ctx->partials.as<double>(), *rr2 = rr + kRedBlocks, *pap = rr + 2 * kRedBlocks,
-         *bb = rr + 3 * kRedBlocks;
+  double *rr = ctx->admm_partials.as<double>(), *rr2 = rr + np, *pap = rr + 2 * np,
+         *bb = rr + 3 * np;
   float *const pix = ctx->r.as<float>();
   const uint32_t *bits = ctx->bits.as<uint32_t>();
   const float frho = (float)rho;
-  const int64_t *off = reinterpret_cast<const int64_t *>(bc.host.data());
-  // One image at a time: the CG scalars are per image, as in the per-image
-  // solver of the paper.  Vectors use the batch's code layout.
-  for (int i = 0; i < b.n; ++i) {
-    const BatchDev v = image_view(bc, i);
-    const int64_t o = off[i] * K, n = v.total_px * K;
-    const uint32_t *bi = bits + off[i] * KW;
-    float *zi = z_dev + o;
-    // QP operator: out = m (D^T D (m in)) + rho m in
-    auto apply_qp = [&](const float *in_global, float *out_global) -> scsc_status {
-      CK(launch_synth_fp32(v, K, s, d_dev, in_global, bits, nullptr, pix, st));
-      CK(launch_adjoint_fp32(v, K, s, d_dev, pix, bits, 0, nullptr, out_global, st));
-      CK(launch_admm_qp_finish(in_global + o, out_global + o, bi, K, frho, n, st));
-      return SCSC_OK;
-    };
-    CK(launch_admm_init(zi, y + o, u + o, bi, K, n, st));
-    CK(launch_adjoint_fp32(v, K, s, d_dev, x_dev, nullptr, 0, nullptr, atx, st));
-    for (int it = 0; it < n_iters; ++it) {
-      CK(launch_admm_rhs(atx + o, y + o, u + o, bv + o, bi, K, frho, n, st));
-      CKS(apply_qp(z_dev, Ap));
-      CK(launch_cg_init(bv + o, Ap + o, res + o, pv + o, n, st));
-      CK(launch_dot_partials(res + o, res + o, n, rr, kRedBlocks, st));
-      CK(launch_dot_partials(bv + o, bv + o, n, bb, kRedBlocks, st));
-      for (int k = 0; k < cg_iters; ++k) {
-        CKS(apply_qp(pv, Ap));
-        CK(launch_dot_partials(pv + o, Ap + o, n, pap, kRedBlocks, st));
-        CK(launch_cg_step(zi, res + o, pv + o, Ap + o, rr, pap, bb, kRedBlocks, n, st));
-        CK(launch_dot_partials(res + o, res + o, n, rr2, kRedBlocks, st));
-        CK(launch_cg_direction(pv + o, res + o, rr2, rr, bb, kRedBlocks, n, st));
-        std::swap(rr, rr2);
-      }
-      CK(launch_admm_shrink(zi, y + o, u + o, bi, K, (float)alpha_r,
-                            (float)(ctx->cfg.lambda / rho), n, st));
+  // Every image runs its own CG (per-image scalars, as in the per-image solver
+  // of the paper); each launch covers the whole batch.
+  // QP operator: out = m (D^T D (m in)) + rho m in
+  auto apply_qp = [&](const float *in, float *out) -> scsc_status {
+    int p1 = ctx->prof.begin(KID_SYNTH_FP32, st);
+    CK(launch_synth_fp32(b, K, s, d_dev, in, bits, nullptr, pix, st));
+    ctx->prof.end(p1, st);
+    int p2 = ctx->prof.begin(KID_ADJ_FP32, st);
+    CK(launch_adjoint_fp32(b, K, s, d_dev, pix, bits, 0, nullptr, out, st));
+    ctx->prof.end(p2, st);
+    CK(launch_admm_qp_finish(b, K, in, out, bits, frho, st));
+    return SCSC_OK;
+  };
+  CK(launch_admm_init(b, K, z_dev, y, u, bits, st));
+  CK(launch_adjoint_fp32(b, K, s, d_dev, x_dev, nullptr, 0, nullptr, atx, st));
+  for (int it = 0; it < n_iters; ++it) {
+    CK(launch_admm_rhs(b, K, atx, y, u, bv, bits, frho, st));
+    CKS(apply_qp(z_dev, Ap));
+    CK(launch_cg_init(b, K, bv, Ap, res, pv, st));
+    CK(launch_seg_dot(b, K, res, res, rr, st));
+    CK(launch_seg_dot(b, K, bv, bv, bb, st));
+    for (int k = 0; k < cg_iters; ++k) {
+      CKS(apply_qp(pv, Ap));
+      CK(launch_seg_dot(b, K, pv, Ap, pap, st));
+      CK(launch_cg_step(b, K, z_dev, res, pv, Ap, rr, pap, bb, st));
+      CK(launch_seg_dot(b, K, res, res, rr2, st));
+      CK(launch_cg_direction(b, K, pv, res, rr2, rr, bb, st));
+      std::swap(rr, rr2);
     }
-    CK(launch_admm_final(zi, y + o, bi, K, n, st));
+    CK(launch_admm_shrink(b, K, z_dev, y, u, bits, (float)alpha_r,
+                          (float)(ctx->cfg.lambda / rho), st));
   }
+  CK(launch_admm_final(b, K, z_dev, y, bits, st));
   return SCSC_OK;
 }
 

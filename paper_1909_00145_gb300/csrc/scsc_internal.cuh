@@ -91,25 +91,31 @@ cudaError_t launch_sum_sq_abs(const float *a, int64_t n_sq, const float *b, int6
                               double *partials, int n_blocks, cudaStream_t st);
 cudaError_t launch_finish_sum(const double *partials, int n_blocks, double scale_sq,
                               double scale_abs, double *out, cudaStream_t st);
-// ADMM vector steps (kernels_admm.cu); n = codes of one image, bits = its M^t.
-cudaError_t launch_admm_init(float *z, float *y, float *u, const uint32_t *bits, int K, int64_t n,
-                             cudaStream_t st);
-cudaError_t launch_admm_rhs(const float *atx, const float *y, const float *u, float *b,
-                            const uint32_t *bits, int K, float rho, int64_t n, cudaStream_t st);
-cudaError_t launch_admm_qp_finish(const float *in, float *out, const uint32_t *bits, int K,
-                                  float rho, int64_t n, cudaStream_t st);
-cudaError_t launch_cg_init(const float *b, const float *Ap, float *res, float *p, int64_t n,
+// ADMM vector steps over a batch (kernels_admm.cu): 2D grids, y = image, x =
+// kAdmmBlocks blocks; codes in the batch's dense layout, bits = the batch's
+// M^t; dot products as kAdmmBlocks FP64 partials per image.
+constexpr int kAdmmBlocks = 64;
+cudaError_t launch_seg_dot(const BatchDev &b, int K, const float *a, const float *c,
+                           double *partials, cudaStream_t st);
+cudaError_t launch_admm_init(const BatchDev &b, int K, float *z, float *y, float *u,
+                             const uint32_t *bits, cudaStream_t st);
+cudaError_t launch_admm_rhs(const BatchDev &b, int K, const float *atx, const float *y,
+                            const float *u, float *bv, const uint32_t *bits, float rho,
+                            cudaStream_t st);
+cudaError_t launch_admm_qp_finish(const BatchDev &b, int K, const float *in, float *out,
+                                  const uint32_t *bits, float rho, cudaStream_t st);
+cudaError_t launch_cg_init(const BatchDev &b, int K, const float *bv, const float *Ap, float *res,
+                           float *p, cudaStream_t st);
+cudaError_t launch_cg_step(const BatchDev &b, int K, float *z, float *res, const float *p,
+                           const float *Ap, const double *rr, const double *pap, const double *bb,
                            cudaStream_t st);
-cudaError_t launch_cg_step(float *z, float *res, const float *p, const float *Ap,
-                           const double *rr, const double *pap, const double *bb, int nb,
-                           int64_t n, cudaStream_t st);
-cudaError_t launch_cg_direction(float *p, const float *res, const double *rr_new,
-                                const double *rr, const double *bb, int nb, int64_t n,
+cudaError_t launch_cg_direction(const BatchDev &b, int K, float *p, const float *res,
+                                const double *rr_new, const double *rr, const double *bb,
                                 cudaStream_t st);
-cudaError_t launch_admm_shrink(const float *z, float *y, float *u, const uint32_t *bits, int K,
-                               float ar, float tau, int64_t n, cudaStream_t st);
-cudaError_t launch_admm_final(float *z, const float *y, const uint32_t *bits, int K, int64_t n,
-                              cudaStream_t st);
+cudaError_t launch_admm_shrink(const BatchDev &b, int K, const float *z, float *y, float *u,
+                               const uint32_t *bits, float ar, float tau, cudaStream_t st);
+cudaError_t launch_admm_final(const BatchDev &b, int K, float *z, const float *y,
+                              const uint32_t *bits, cudaStream_t st);
 // r[i] = 0 where obs[i] == 0 (observed-pixel data term).
 cudaError_t launch_mask_residual(float *r, const uint8_t *obs, int64_t n, cudaStream_t st);
 // D D^T of the step-size domain as per-class stencils (kernels_ddt.cu):
