@@ -253,6 +253,36 @@ def dict_step_batch(cfg: Config, batch: Batch, x, z, d) -> np.ndarray:
     return project_filters(dn, cfg.K, M)
 
 
+def dict_step_gauss_seidel(cfg: Config, batch: Batch, x, z, d) -> np.ndarray:
+    """Eq. 5 by one pass of projected block coordinate descent (Sec. 3.2): for
+    k = 1..K in order, G_k = sum_n Z_{n,k}^T r_n with the current residuals,
+    d_k <- P(d_k - G_k / L_d), then r_n <- r_n + Z_{n,k} (d_k^new - d_k^old).
+    L_d is the batch step's power-iteration estimate of lambda_max(sum_n
+    Z_n^T Z_n), an upper bound of every block's lambda_max(Z_k^T Z_k)."""
+    d = _f64(d).ravel().copy()
+    x, z = _f64(x), _f64(z)
+    K, s = cfg.K, cfg.s
+    M = s * s
+    L = lipschitz_filters(cfg, batch, z)
+    r = [synthesis(d, batch.image(z, n, K), K, s, int(batch.H[n]), int(batch.W[n]))
+         - batch.image(x, n) for n in range(batch.n)]
+    for k in range(K):
+        G = np.zeros(M)
+        for n in range(batch.n):
+            H, W = int(batch.H[n]), int(batch.W[n])
+            G += filter_gradient(r[n], batch.image(z, n, K), K, s, H, W)[k * M:(k + 1) * M]
+        old = d[k * M:(k + 1) * M].copy()
+        new = old - G / L if L > 0 else old.copy()
+        new = project_filters(new, 1, M)
+        delta = np.zeros(K * M)
+        delta[k * M:(k + 1) * M] = new - old
+        for n in range(batch.n):
+            H, W = int(batch.H[n]), int(batch.W[n])
+            r[n] = r[n] + synthesis(delta, batch.image(z, n, K), K, s, H, W)
+        d[k * M:(k + 1) * M] = new
+    return d
+
+
 class OnlineState:
     """Surrogates C^t, B^t of Eq. 7 (mean over the mini-batch) and Eq. 8."""
 

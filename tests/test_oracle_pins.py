@@ -435,3 +435,54 @@ def test_observed_pg_step_matches_explicit_matrices_8x8():
     f = R.objective_observed(cfg, batch, x, z1, d, obs)
     assert f == pytest.approx(0.5 * np.sum(obs * (x - A @ z1) ** 2) + cfg.lam * np.abs(z1).sum(),
                               rel=1e-13)
+
+
+# ------------------------------------------------------------------ Gauss-Seidel dictionary pass
+
+def test_gauss_seidel_with_one_filter_is_the_jacobi_step():
+    K, s, H, W = 1, 5, 14, 12
+    x, d = I.images(3, [H], [W]).astype(np.float64), I.filters(4, K, s).astype(np.float64)
+    z = I.sparse_codes(5, H * W, K, density=0.2).astype(np.float64)
+    cfg = R.Config(K=K, s=s, seed=2)
+    batch = R.Batch(H=[H], W=[W], ids=[0])
+    np.testing.assert_allclose(R.dict_step_gauss_seidel(cfg, batch, x, z, d),
+                               R.dict_step_batch(cfg, batch, x, z, d), rtol=0, atol=1e-14)
+
+
+def test_gauss_seidel_equals_jacobi_when_blocks_do_not_interact():
+    """Filters whose code maps lie far apart (more than 2(s-1) pixels) have
+    Z_j^T Z_k = 0: each block's residual update leaves the next blocks'
+    gradients unchanged, so one sequential pass equals the simultaneous step."""
+    K, s, H, W = 2, 5, 10, 30
+    d = I.filters(6, K, s).astype(np.float64)
+    x = I.images(7, [H], [W]).astype(np.float64)
+    z = np.zeros((H, W, K))
+    z[:, :8, 0] = rng(1).normal(size=(H, 8))
+    z[:, 20:, 1] = rng(2).normal(size=(H, 10))
+    cfg = R.Config(K=K, s=s, seed=3)
+    batch = R.Batch(H=[H], W=[W], ids=[0])
+    np.testing.assert_allclose(R.dict_step_gauss_seidel(cfg, batch, x, z.ravel(), d),
+                               R.dict_step_batch(cfg, batch, x, z.ravel(), d), atol=1e-13)
+
+
+def test_gauss_seidel_matches_explicit_matrices_and_descends():
+    K, s, H, W = 3, 5, 8, 8
+    d = I.filters(8, K, s).astype(np.float64).ravel()
+    x = I.images(9, [H], [W]).astype(np.float64)
+    z = rng(10).normal(size=H * W * K)
+    cfg = R.Config(K=K, s=s, seed=4)
+    batch = R.Batch(H=[H], W=[W], ids=[0])
+    got = R.dict_step_gauss_seidel(cfg, batch, x, z, d)
+    Z = explicit_code_matrix(z, K, s, H, W)
+    L = R.lipschitz_filters(cfg, batch, z)
+    M = s * s
+    want = d.copy()
+    f0 = 0.5 * np.sum((Z @ want - x) ** 2)
+    for k in range(K):
+        g = Z[:, k * M:(k + 1) * M].T @ (Z @ want - x)
+        v = want[k * M:(k + 1) * M] - g / L
+        want[k * M:(k + 1) * M] = v / max(1.0, np.linalg.norm(v))
+        f1 = 0.5 * np.sum((Z @ want - x) ** 2)
+        assert f1 <= f0 * (1 + 1e-12)  # a step of 1/L on one block never increases Eq. 5
+        f0 = f1
+    np.testing.assert_allclose(got, want, atol=1e-12)
