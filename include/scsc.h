@@ -51,9 +51,11 @@ typedef enum {
 } scsc_precision;
 
 typedef enum {
-  SCSC_DICT_BATCH = 0, /* Eq. 5, one projected-gradient step (Alg. 1 line 8)   */
-  SCSC_DICT_ONLINE = 1 /* Eq. 7 surrogate update + one projected-gradient step
-                          on Eq. 8 (Alg. 2 lines 8-9)                          */
+  SCSC_DICT_BATCH = 0,   /* Eq. 5, one projected-gradient step (Alg. 1 line 8) */
+  SCSC_DICT_ONLINE = 1,  /* Eq. 7 surrogate update + one projected-gradient step
+                            on Eq. 8 (Alg. 2 lines 8-9)                        */
+  SCSC_DICT_BATCH_GS = 2 /* Eq. 5, one Gauss-Seidel pass of projected block
+                            coordinate descent over the filters (Sec. 3.2)     */
 } scsc_dict_mode;
 
 typedef struct {
@@ -151,6 +153,9 @@ scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const fl
  * G_k(u,v) = sum_n sum_{i,j} r(i,j) z_k(i+c-u, j+c-v),
  * d_k <- P(d_k - G_k / L_d) with L_d from the power-iteration rule on
  * sum_n Z_n^T Z_n and P the projection onto ||d_k|| <= 1.
+ * SCSC_DICT_BATCH_GS (Eq. 5, Sec. 3.2): the same L_d, then for k = 0..K-1 in
+ * order: G_k from the current residual, d_k <- P(d_k - G_k / L_d), and the
+ * residual r <- r + Z_k (d_k^new - d_k^old) before the next filter.
  * SCSC_DICT_ONLINE (Eq. 7-8, t >= 1 counts mini-batches): C, B <- (t-1)/t
  * C, B + (1/t) mean_n Z_n^T Z_n, Z_n^T x_n; d <- P(d - (C d - B) / L_C). */
 scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,

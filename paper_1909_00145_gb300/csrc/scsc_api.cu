@@ -614,7 +614,7 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
                            const float *z_dev, float *d_dev, scsc_dict_mode mode, uint64_t t) {
   if (!ctx) return SCSC_EINVAL;
   if (!x_dev || !z_dev || !d_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
-  if (mode != SCSC_DICT_BATCH && mode != SCSC_DICT_ONLINE)
+  if (mode != SCSC_DICT_BATCH && mode != SCSC_DICT_ONLINE && mode != SCSC_DICT_BATCH_GS)
     return fail(ctx, SCSC_EINVAL, "unknown dictionary mode %d", (int)mode);
   CKS(stage_batch(ctx, batch));
   const BatchDev &b = ctx->batch.view;
@@ -635,6 +635,21 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
                         nullptr, 0.0));
     CK(launch_project_step(d_dev, nullptr, ctx->Cd.as<double>(), ctx->scal.as<double>() + 1, K, M,
                            st));
+    return SCSC_OK;
+  }
+  if (mode == SCSC_DICT_BATCH_GS) {
+    CK(ctx->r.ensure((size_t)b.total_px * 4));
+    CK(ctx->pix2.ensure((size_t)b.total_px * 4));
+    CK(ctx->gpart.ensure((size_t)(kGradGroups + 1) * M * 4));
+    CKS(power_iteration(ctx, (int64_t)K * M, kTagLd,
+                        [&](const float *u, float *w) { return apply_ztz(ctx, z_dev, u, w); }, 1,
+                        nullptr, 0.0));
+    // r = D z - x, then the blocks in order; the residual follows each block
+    CK(launch_synth_fp32(b, K, s, d_dev, z_dev, nullptr, x_dev, ctx->r.as<float>(), st));
+    float *partial = ctx->gpart.as<float>(), *delta = partial + (size_t)kGradGroups * M;
+    for (int k = 0; k < K; ++k)
+      CK(launch_gs_block(b, K, s, k, d_dev, z_dev, ctx->r.as<float>(), ctx->scal.as<double>() + 1,
+                         partial, kGradGroups, delta, st));
     return SCSC_OK;
   }
   // Online (Eq. 7, Eq. 8)

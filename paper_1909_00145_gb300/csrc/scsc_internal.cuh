@@ -116,6 +116,12 @@ cudaError_t launch_admm_shrink(const BatchDev &b, int K, const float *z, float *
                                const uint32_t *bits, float ar, float tau, cudaStream_t st);
 cudaError_t launch_admm_final(const BatchDev &b, int K, float *z, const float *y,
                               const uint32_t *bits, cudaStream_t st);
+// One Gauss-Seidel block (filter k) of the dictionary pass (kernels_gs.cu):
+// gradient of block k from residual r, d_k <- P(d_k - G_k / *L), r += Z_k delta.
+// partial: n_groups * s * s floats; delta: s * s floats.
+cudaError_t launch_gs_block(const BatchDev &b, int K, int s, int k, float *d, const float *z,
+                            float *r, const double *L, float *partial, int n_groups, float *delta,
+                            cudaStream_t st);
 // r[i] = 0 where obs[i] == 0 (observed-pixel data term).
 cudaError_t launch_mask_residual(float *r, const uint8_t *obs, int64_t n, cudaStream_t st);
 // D D^T of the step-size domain as per-class stencils (kernels_ddt.cu):

@@ -25,7 +25,7 @@ SCSC_OK, SCSC_EINVAL, SCSC_ENOMEM, SCSC_ECUDA, SCSC_ETIMEOUT, SCSC_ENONFINITE, S
 STATUS_NAMES = ["SCSC_OK", "SCSC_EINVAL", "SCSC_ENOMEM", "SCSC_ECUDA", "SCSC_ETIMEOUT",
                 "SCSC_ENONFINITE", "SCSC_EUNSUPPORTED"]
 SCSC_FP32, SCSC_BF16 = 0, 1
-SCSC_DICT_BATCH, SCSC_DICT_ONLINE = 0, 1
+SCSC_DICT_BATCH, SCSC_DICT_ONLINE, SCSC_DICT_BATCH_GS = 0, 1, 2
 SCSC_FLAG_PER_IMAGE, SCSC_FLAG_NO_GRAPH, SCSC_FLAG_NO_AUTOTUNE = 1, 2, 4
 
 

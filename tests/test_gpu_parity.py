@@ -240,3 +240,24 @@ def test_code_step_many_items_per_cta(prec):
     zg, zo, fg, fo, _ = run_code_step(prec, 32, 7, H, W, (1, 4), 6, seed=6, lam=0.7)
     assert fg == pytest.approx(fo, rel=1e-5 if prec == "fp32" else 1e-3)
     assert rel_l2(zg, zo) < (1e-4 if prec == "fp32" else 5e-2)
+
+
+@pytest.mark.parametrize("K,s,H,W", [(12, 11, [40, 33], [50, 61]), (20, 5, [37, 64], [131, 64]),
+                                     (5, 3, [9], [12])])
+def test_dict_step_gauss_seidel_fp32(K, s, H, W):
+    """One Gauss-Seidel pass of projected block coordinate descent (Sec. 3.2)
+    against the oracle: every block sees the residual of the blocks before."""
+    x, d, z = make_case(H, W, K, s, seed=16, code_density=0.08)
+    ids = list(range(len(H)))
+    cfg = R.Config(K=K, s=s, seed=71)
+    rb = R.Batch(H=H, W=W, ids=ids)
+    do = R.dict_step_gauss_seidel(cfg, rb, x, z, d)
+    ctx = scsc.Context(K, s, seed=71)
+    b = scsc.Batch(H, W)
+    dt = dev(d)
+    ctx.dict_step(b, dev(x), dev(z), dt, scsc.SCSC_DICT_BATCH_GS, 1)
+    assert rel_l2(host(dt), do) < 1e-4
+    assert np.all(np.linalg.norm(host(dt).reshape(K, -1), axis=1) <= 1 + 1e-6)
+    # and it differs from the simultaneous (Jacobi) step
+    dj = R.dict_step_batch(cfg, rb, x, z, d)
+    assert rel_l2(do, dj) > 10 * rel_l2(host(dt), do)
