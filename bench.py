@@ -304,6 +304,41 @@ def accuracy_report(n_images=4):
                       "oracle_seconds": oracle_s}), flush=True)
 
 
+def dict_report(steps=5):
+    """Time the dictionary steps (Eq. 5: simultaneous projected gradient, and
+    the Gauss-Seidel pass over the filters) on the 64 x 256^2 workload with
+    the codes of one code step; one JSON line."""
+    import torch
+    from paper_1909_00145_gb300 import scsc
+    wl = WORKLOADS["c3"]
+    H, W, ids, x_np, d_np = make_inputs(wl, 0)
+    K = wl["K"]
+    stream = torch.cuda.Stream()
+    ctx = scsc.Context(K, 11, 1.0, wl["p"], seed=0, prec="bf16", stream=stream)
+    batch = scsc.Batch(H, W, ids)
+    x = torch.from_numpy(x_np).cuda()
+    d0 = torch.from_numpy(d_np).cuda().contiguous()
+    z = torch.zeros(batch.total_pixels * K, device="cuda")
+    out = {"workload": "dictionary steps on " + wl["desc"], "n_gpus": 1, "steps": steps}
+    with torch.cuda.stream(stream):
+        ctx.code_step(batch, x, d0, z, 1, wl["n_iters"])
+        for name, mode in [("jacobi", scsc.SCSC_DICT_BATCH), ("gauss_seidel", scsc.SCSC_DICT_BATCH_GS)]:
+            d = d0.clone()
+            ctx.dict_step(batch, x, z, d, mode, 1)  # warm-up
+            ctx.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                ctx.dict_step(batch, x, z, d, mode, 1)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            f = ctx.objective(batch, x, z, d)
+            out[name] = {"ms_per_step": ms, "objective_after": f}
+        out["objective_before"] = ctx.objective(batch, x, z, d0)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,9 +357,14 @@ def main():
                     help="tensor path: launch iterations directly instead of replaying a graph")
     ap.add_argument("--accuracy", action="store_true",
                     help="print the BF16 / FP32 errors against the FP64 oracle on 4 images and exit")
+    ap.add_argument("--dict", action="store_true",
+                    help="time the Jacobi and Gauss-Seidel dictionary steps and exit")
     args = ap.parse_args()
     if args.accuracy:
         accuracy_report()
+        return
+    if args.dict:
+        dict_report()
         return
     if args.warmup < 3:
         args.warmup = 3
