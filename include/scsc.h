@@ -119,6 +119,19 @@ scsc_status scsc_mask(scsc_ctx *ctx, const scsc_batch *batch, uint64_t t, uint32
 scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
                            const float *d_dev, float *z_dev, uint64_t t, int n_iters);
 
+/* scsc_code_step on HOST buffers: x_host (packed images), d_host (K x s x s)
+ * and z_host (warm start in, Eq. 4 codes out), all float32 in scsc_code_step's
+ * layouts.  The step size is taken once for the whole batch; the images are
+ * then processed in up to 4 contiguous chunks (at least 2^20 pixels each), and
+ * chunk c + 1's host-to-device copy and chunk c - 1's device-to-host copy run
+ * on their own streams while chunk c computes.  Results equal scsc_code_step's
+ * (every image's update is independent of the others).  Page-locked host
+ * memory is needed for the copies to overlap (pageable memory is correct but
+ * serialises them).  Returns once z_host holds the result.  Errors as
+ * scsc_code_step. */
+scsc_status scsc_code_step_host(scsc_ctx *ctx, const scsc_batch *batch, const float *x_host,
+                                const float *d_host, float *z_host, uint64_t t, int n_iters);
+
 /* Inpainting (Sec. 4.3: reconstruction from partially observed pixels): the
  * code update of scsc_code_step with the data term counted on observed pixels
  * only, 1/2 || O (x - D (M^t)^T z~) ||^2, O = diag(observed), so the residual

@@ -671,8 +671,10 @@ int *tc_error_word(TcWorkspace &ws) {
 const char *tc_last_error(const TcWorkspace &ws) { return ws.last_error.c_str(); }
 
 void tc_release(TcWorkspace &ws) {
-  if (ws.graph_exec) cudaGraphExecDestroy(ws.graph_exec);
-  ws.graph_exec = nullptr;
+  for (GraphSlot &g : ws.graphs_cached) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+  }
   for (TcWorkspace::Buf *b : {&ws.item0, &ws.seg_count, &ws.seg_base, &ws.pxoff, &ws.scan_blocks,
                               &ws.packed, &ws.xcore, &ws.spill, &ws.r, &ws.badj, &ws.bsyn,
                               &ws.err}) {
@@ -875,24 +877,52 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   const bool use_graph = ws.graphs && rem > 0 && st != nullptr && !user_capture &&
                          !(ws.prof && ws.prof->on);
   if (use_graph) {
-    const GraphKey gk{bits, seg_base, pxoff, ws.packed.p, ws.bsyn.p, ws.badj.p, ws.xcore.p,
-                      ws.spill.p, ws.r.p, ws.err.p, x, prm, ws.item0.p, b.off, obs, K, s,
-                      Q, variant, rem};
-    if (!ws.graph_exec || std::memcmp(&gk, &ws.graph_key, sizeof gk) != 0) {
-      if (ws.graph_exec) cudaGraphExecDestroy(ws.graph_exec);
-      ws.graph_exec = nullptr;
+    GraphKey gk{};  // zero-filled, so that memcmp sees no padding bytes
+    gk.bits = bits;
+    gk.seg_base = seg_base;
+    gk.pxoff = pxoff;
+    gk.packed = ws.packed.p;
+    gk.bsyn = ws.bsyn.p;
+    gk.badj = ws.badj.p;
+    gk.xcore = ws.xcore.p;
+    gk.spill = ws.spill.p;
+    gk.r = ws.r.p;
+    gk.err = ws.err.p;
+    gk.x = x;
+    gk.prm = prm;
+    gk.item0 = ws.item0.p;
+    gk.off = b.off;
+    gk.obs = obs;
+    gk.total_px = b.total_px;
+    gk.n_images = b.n;
+    gk.K = K;
+    gk.s = s;
+    gk.Q = Q;
+    gk.variant = variant;
+    gk.iters = rem;
+    GraphSlot *slot = nullptr;
+    for (GraphSlot &g : ws.graphs_cached)
+      if (g.exec && std::memcmp(&gk, &g.key, sizeof gk) == 0) slot = &g;
+    if (!slot) {
+      // capture into the least recently used slot
+      slot = &ws.graphs_cached[0];
+      for (GraphSlot &g : ws.graphs_cached)
+        if (!g.exec || g.used < slot->used) slot = &g;
+      if (slot->exec) cudaGraphExecDestroy(slot->exec);
+      slot->exec = nullptr;
       cudaGraph_t g = nullptr;
       TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
       cudaError_t err = cudaSuccess;
       for (int it = 0; it < rem && err == cudaSuccess; ++it) err = iteration(variant);
       cudaError_t e2 = cudaStreamEndCapture(st, &g);
       if (err == cudaSuccess) err = e2;
-      if (err == cudaSuccess) err = cudaGraphInstantiate(&ws.graph_exec, g, 0);
+      if (err == cudaSuccess) err = cudaGraphInstantiate(&slot->exec, g, 0);
       if (g) cudaGraphDestroy(g);
       TRY(err);
-      ws.graph_key = gk;
+      slot->key = gk;
     }
-    TRY(cudaGraphLaunch(ws.graph_exec, st));
+    slot->used = ++ws.graph_clock;
+    TRY(cudaGraphLaunch(slot->exec, st));
   } else {
     for (int it = 0; it < rem; ++it) TRY(iteration(variant));
   }

@@ -76,6 +76,12 @@ struct scsc_ctx {
   DevBuf ddtG, ddtA;  // tap Gram matrix and per-class stencils of D D^T
   DevBuf admm;        // ADMM vectors: y, u, b, A^T x, CG residual, direction, QP image
   DevBuf admm_partials;  // per-image FP64 partials of the CG dot products
+  // host-buffer entry: device copies of d and of two chunks of x and z, the
+  // copy streams and the events that order them
+  DevBuf hd, hx[2], hz[2];
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr},
+              ev_out[2] = {nullptr, nullptr};
   // tensor path
   TcWorkspace tc;
   // online surrogates
@@ -366,6 +372,7 @@ scsc_status scsc_destroy(scsc_ctx *ctx) {
   for (DevBuf *b : {&ctx->bits, &ctx->r, &ctx->pix2, &ctx->prm, &ctx->scal, &ctx->partials,
                     &ctx->gpart, &ctx->gsum, &ctx->pu, &ctx->pw,
                     &ctx->flag, &ctx->ddtG, &ctx->ddtA, &ctx->admm, &ctx->admm_partials,
+                    &ctx->hd, &ctx->hx[0], &ctx->hx[1], &ctx->hz[0], &ctx->hz[1],
                     &ctx->C, &ctx->B, &ctx->Cd, &ctx->batch.dev, &ctx->domain.dev})
     b->release();
   for (BatchCache *bc : {&ctx->batch, &ctx->domain}) {
@@ -374,6 +381,11 @@ scsc_status scsc_destroy(scsc_ctx *ctx) {
   }
   tc_release(ctx->tc);
   ctx->prof.release();
+  for (cudaStream_t *sp : {&ctx->s_in, &ctx->s_out})
+    if (*sp) cudaStreamDestroy(*sp);
+  for (int i = 0; i < 2; ++i)
+    for (cudaEvent_t e : {ctx->ev_in[i], ctx->ev_done[i], ctx->ev_out[i]})
+      if (e) cudaEventDestroy(e);
   delete ctx;
   return SCSC_OK;
 }
@@ -406,9 +418,11 @@ scsc_status scsc_lipschitz_codes(scsc_ctx *ctx, const scsc_batch *batch, const f
 }
 
 // scsc_code_step / scsc_code_step_observed (obs = NULL: every pixel observed).
+// keep_step: use the step parameters already in ctx->prm (the host-buffer
+// entry computes them once for the whole batch before its chunks).
 static scsc_status code_step_impl(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
                            const float *d_dev, float *z_dev, const uint8_t *obs, uint64_t t,
-                           int n_iters) {
+                           int n_iters, bool keep_step = false) {
   if (!ctx) return SCSC_EINVAL;
   if (!x_dev || !d_dev || !z_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
   if (n_iters < 0) return fail(ctx, SCSC_EINVAL, "n_iters = %d < 0", n_iters);
@@ -417,7 +431,7 @@ static scsc_status code_step_impl(scsc_ctx *ctx, const scsc_batch *batch, const 
   const int K = ctx->cfg.K, s = ctx->cfg.s;
   cudaStream_t st = ctx->stream;
   CKS(build_mask(ctx, t));
-  CKS(code_step_size(ctx, d_dev));
+  if (!keep_step) CKS(code_step_size(ctx, d_dev));
   const StepParams *prm = ctx->prm.as<StepParams>();
   if (ctx->cfg.prec == SCSC_BF16) {
     int *errw = tc_error_word(ctx->tc);
@@ -486,6 +500,88 @@ static scsc_status objective_impl(scsc_ctx *ctx, const scsc_batch *batch, const 
 scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
                            const float *d_dev, float *z_dev, uint64_t t, int n_iters) {
   return code_step_impl(ctx, batch, x_dev, d_dev, z_dev, nullptr, t, n_iters);
+}
+
+scsc_status scsc_code_step_host(scsc_ctx *ctx, const scsc_batch *batch, const float *x_host,
+                                const float *d_host, float *z_host, uint64_t t, int n_iters) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!x_host || !d_host || !z_host) return fail(ctx, SCSC_EINVAL, "NULL host pointer");
+  if (n_iters < 0) return fail(ctx, SCSC_EINVAL, "n_iters = %d < 0", n_iters);
+  if (!batch || batch->n_images < 1) return fail(ctx, SCSC_EINVAL, "batch: n_images must be >= 1");
+  const int K = ctx->cfg.K, M = M_of(ctx), n = batch->n_images;
+  cudaStream_t st = ctx->stream;
+  if (!ctx->s_in) {
+    CK(cudaStreamCreateWithFlags(&ctx->s_in, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->s_out, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      CK(cudaEventCreateWithFlags(&ctx->ev_in[i], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_done[i], cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_out[i], cudaEventDisableTiming));
+    }
+  }
+  // the step size of the whole batch (max H x max W domain), once
+  CK(ctx->hd.ensure((size_t)K * M * 4));
+  CK(cudaMemcpyAsync(ctx->hd.p, d_host, (size_t)K * M * 4, cudaMemcpyHostToDevice, st));
+  const float *d_dev = ctx->hd.as<float>();
+  CKS(stage_batch(ctx, batch));
+  CKS(code_step_size(ctx, d_dev));
+  // chunks: contiguous image ranges of about equal pixel counts, at least
+  // 2^20 pixels each, at most 4 (the first chunk's copy in and the last one's
+  // copy out are the parts that do not overlap; more chunks add per-call work)
+  int64_t total = 0;
+  for (int i = 0; i < n; ++i) total += (int64_t)batch->H[i] * batch->W[i];
+  const int want = (int)std::max<int64_t>(1, std::min<int64_t>({4, n, total >> 20}));
+  std::vector<int> first{0};  // chunk c = images [first[c], first[c + 1])
+  {
+    int64_t acc = 0;
+    for (int i = 0; i < n; ++i) {
+      acc += (int64_t)batch->H[i] * batch->W[i];
+      if (i + 1 < n && (int)first.size() < want && acc * want >= total * (int64_t)first.size())
+        first.push_back(i + 1);
+    }
+    first.push_back(n);
+  }
+  const int nch = (int)first.size() - 1;
+  int64_t max_px = 0;
+  for (int c = 0; c < nch; ++c) max_px = std::max(max_px, batch->offsets[first[c + 1] - 1] +
+                                                              (int64_t)batch->H[first[c + 1] - 1] *
+                                                                  batch->W[first[c + 1] - 1] -
+                                                              batch->offsets[first[c]]);
+  for (int i = 0; i < 2 && i < nch; ++i) {
+    CK(ctx->hx[i].ensure((size_t)max_px * 4));
+    CK(ctx->hz[i].ensure((size_t)max_px * K * 4));
+  }
+  // Chunk c uses slot c % 2: copy in on s_in (after the slot's previous
+  // chunk has been copied out), compute on the context stream, copy out on
+  // s_out; chunk c + 1's copy in overlaps chunk c's compute.
+  std::vector<int64_t> off_c;
+  scsc_status status = SCSC_OK;
+  for (int c = 0; c < nch && status == SCSC_OK; ++c) {
+    const int i0 = first[c], i1 = first[c + 1], slot = c & 1;
+    const int64_t o = batch->offsets[i0];
+    const int64_t px = batch->offsets[i1 - 1] + (int64_t)batch->H[i1 - 1] * batch->W[i1 - 1] - o;
+    if (c >= 2) CK(cudaStreamWaitEvent(ctx->s_in, ctx->ev_out[slot], 0));
+    CK(cudaMemcpyAsync(ctx->hx[slot].p, x_host + o, (size_t)px * 4, cudaMemcpyHostToDevice,
+                       ctx->s_in));
+    CK(cudaMemcpyAsync(ctx->hz[slot].p, z_host + o * K, (size_t)px * K * 4,
+                       cudaMemcpyHostToDevice, ctx->s_in));
+    CK(cudaEventRecord(ctx->ev_in[slot], ctx->s_in));
+    CK(cudaStreamWaitEvent(st, ctx->ev_in[slot], 0));
+    off_c.assign(i1 - i0, 0);
+    for (int i = i0; i < i1; ++i) off_c[i - i0] = batch->offsets[i] - o;
+    const scsc_batch cb{i1 - i0, off_c.data(), batch->H + i0, batch->W + i0, batch->image_ids + i0};
+    status = code_step_impl(ctx, &cb, ctx->hx[slot].as<float>(), d_dev, ctx->hz[slot].as<float>(),
+                            nullptr, t, n_iters, /*keep_step=*/true);
+    if (status != SCSC_OK) break;
+    CK(cudaEventRecord(ctx->ev_done[slot], st));
+    CK(cudaStreamWaitEvent(ctx->s_out, ctx->ev_done[slot], 0));
+    CK(cudaMemcpyAsync(z_host + o * K, ctx->hz[slot].p, (size_t)px * K * 4,
+                       cudaMemcpyDeviceToHost, ctx->s_out));
+    CK(cudaEventRecord(ctx->ev_out[slot], ctx->s_out));
+  }
+  CK(cudaStreamSynchronize(ctx->s_out));
+  CK(cudaStreamSynchronize(st));
+  return status;
 }
 
 scsc_status scsc_code_step_observed(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,

@@ -20,12 +20,23 @@ struct TuneKey {
   }
 };
 
-// Everything a captured iteration graph depends on.
+// Everything a captured iteration graph depends on (the buffers it names and
+// the by-value launch arguments that follow from the batch shape).
 struct GraphKey {
   const void *bits, *seg_base, *pxoff, *packed, *bsyn, *badj, *xcore, *spill, *r, *err, *x, *prm,
       *item0, *off, *obs;
-  int K, s, Q, variant, iters;
+  int64_t total_px;
+  int n_images, K, s, Q, variant, iters;
 };
+
+// A few captured graphs, reused while their key matches (the host-buffer
+// entry alternates between two chunk buffers).
+struct GraphSlot {
+  GraphKey key{};
+  cudaGraphExec_t exec = nullptr;
+  uint64_t used = 0;
+};
+constexpr int kGraphSlots = 4;
 
 // Workspace of the tensor path, owned by the context.
 struct TcWorkspace {
@@ -43,8 +54,8 @@ struct TcWorkspace {
   bool autotune = true, graphs = true;
   std::map<TuneKey, int> tune;                       // chosen variant per key
   std::map<TuneKey, std::pair<float, float>> tune_ms;  // timings that chose it
-  cudaGraphExec_t graph_exec = nullptr;
-  GraphKey graph_key{};
+  GraphSlot graphs_cached[kGraphSlots];
+  uint64_t graph_clock = 0;
   std::string last_error;
 };
 

@@ -59,6 +59,8 @@ _SIGNATURES = {
                        c_int],
     "scsc_code_step_observed": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p,
                                 c_void_p, c_void_p, c_u64, c_int],
+    "scsc_code_step_host": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p,
+                            c_u64, c_int],
     "scsc_code_step_admm": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p,
                             c_u64, c_int, c_int, c_double, c_double],
     "scsc_dict_step": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p, c_int,
@@ -194,6 +196,9 @@ class Context:
     def code_step_observed(self, batch, x, d, z, observed, t, n_iters):
         return scsc_code_step_observed(self, batch, x, d, z, observed, t, n_iters)
 
+    def code_step_host(self, batch, x, d, z, t, n_iters):
+        return scsc_code_step_host(self, batch, x, d, z, t, n_iters)
+
     def code_step_admm(self, batch, x, d, z, t, n_iters, cg_iters, rho=0.0, alpha=0.0):
         return scsc_code_step_admm(self, batch, x, d, z, t, n_iters, cg_iters, rho, alpha)
 
@@ -270,6 +275,20 @@ def scsc_code_step_observed(ctx: Context, batch: Batch, x, d, z, observed, t: in
     _check(lib().scsc_code_step_observed(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d),
                                          _ptr(z), _ptr(observed) if observed is not None else None,
                                          t, n_iters), ctx.handle, "scsc_code_step_observed")
+
+
+def _host_ptr(t) -> int:
+    """Address of a contiguous CPU float32 tensor (pinned for copy overlap)."""
+    if t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CPU tensor")
+    return t.data_ptr()
+
+
+def scsc_code_step_host(ctx: Context, batch: Batch, x, d, z, t: int, n_iters: int) -> None:
+    """scsc_code_step on host (CPU) tensors; z is updated in place."""
+    _check(lib().scsc_code_step_host(ctx.handle, ctypes.byref(batch.c), _host_ptr(x),
+                                     _host_ptr(d), _host_ptr(z), t, n_iters), ctx.handle,
+           "scsc_code_step_host")
 
 
 def scsc_code_step_admm(ctx: Context, batch: Batch, x, d, z, t: int, n_iters: int,

@@ -72,3 +72,37 @@ def test_autotuned_variants_agree():
     zb, fb, _ = run("bf16", H, W, x, d, K, s, p, 8, flags=scsc.SCSC_FLAG_NO_AUTOTUNE)
     assert fa == pytest.approx(fb, rel=1e-4)
     assert rel_l2(za, zb) < 1e-3
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_host_buffer_entry_equals_device_entry(prec):
+    """scsc_code_step_host (chunks of the batch, copies overlapped with the
+    compute) gives exactly the codes of scsc_code_step on device buffers."""
+    K, s = 24, 11
+    H, W = I.uneven_sizes(9, 80, 120, 400)
+    x = I.images(10, H, W)
+    d = I.filters(11, K, s)
+    npx = int(np.dot(H.astype(np.int64), W))
+    z0 = I.sparse_codes(12, npx, K, density=0.05)
+    ids = np.arange(len(H)) + 3
+    outs = []
+    for host in (False, True):
+        # fixed kernel variant: the autotuner keys on the launch size, which
+        # differs between the whole batch and a chunk
+        ctx = scsc.Context(K, s, lam=0.8, p=(1, 4), seed=13, prec=prec,
+                           flags=scsc.SCSC_FLAG_NO_AUTOTUNE)
+        b = scsc.Batch(H, W, ids=ids)
+        if host:
+            xh = torch.from_numpy(x).pin_memory()
+            dh = torch.from_numpy(np.ascontiguousarray(d)).pin_memory()
+            zh = torch.from_numpy(z0.copy()).pin_memory()
+            ctx.code_step_host(b, xh, dh, zh, 2, 7)
+            outs.append(zh.numpy().copy())
+        else:
+            z = torch.from_numpy(z0.copy()).cuda()
+            ctx.code_step(b, torch.from_numpy(x).cuda(),
+                          torch.from_numpy(np.ascontiguousarray(d)).cuda(), z, 2, 7)
+            ctx.sync()
+            outs.append(z.cpu().numpy())
+    assert b.total_pixels >= 3 << 20  # several chunks
+    assert np.array_equal(outs[0], outs[1])
