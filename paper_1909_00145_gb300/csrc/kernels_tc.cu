@@ -182,6 +182,37 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int K
   }
 }
 
+// Dense BF16 code tile of every row item in the synthesis A-operand layout
+// (K-major cores of 8 pixels x 8 filters; chunk c of 16 filters at c * 4096
+// bytes): the packed sampled codes, zero elsewhere.  One block per item,
+// thread = pixel of the strip.
+__global__ void __launch_bounds__(kThreads) abuf_kernel(ItemMap im, int Kp, int KW,
+                                                        const uint32_t *bits,
+                                                        const uint64_t *seg_base,
+                                                        const uint16_t *pxoff, const float *packed,
+                                                        uint8_t *abuf) {
+  const int q = blockIdx.x, e = threadIdx.x;
+  const Item it = item_of(im, q);
+  const int NC = Kp / 16;
+  const float *src = packed + seg_base[q] + pxoff[(int64_t)q * kStrip + e];
+  uint8_t *tile = abuf + (size_t)q * kStrip * Kp * 2;
+  for (int c = 0; c < NC; ++c) {
+    const uint32_t m = chunk_mask(bits, KW, it, it.a, it.js * kStrip + e, c);
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      v[j] = ((m >> j) & 1u) ? *src : 0.0f;
+      src += (m >> j) & 1u;
+    }
+    uint8_t *dst = tile + (size_t)(2 * c) * 2048 + (e >> 3) * 128 + (e & 7) * 16;
+    *reinterpret_cast<uint4 *>(dst) = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                                 pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+    *reinterpret_cast<uint4 *>(dst + 2048) =
+        make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]), pack_bf16x2(v[12], v[13]),
+                   pack_bf16x2(v[14], v[15]));
+  }
+}
+
 // ------------------------------------------------------------------ synthesis
 
 template <int S>
@@ -653,14 +684,14 @@ T *as(const TcWorkspace::Buf &b) {
 
 }  // namespace
 
-cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
-                        const uint64_t *seg_base, const uint16_t *pxoff, const float *packed,
+cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint8_t *abuf,
                         const uint4 *bsyn, float *xcore, float *spill, int *err, int grid,
                         int max_smem, cudaStream_t st);
 cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
                         const uint64_t *seg_base, const uint16_t *pxoff, float *packed,
-                        const uint4 *badj, const float *r, const StepParams *prm, int *err,
-                        int grid, cudaStream_t st);
+                        uint8_t *abuf, const uint4 *badj, const float *r, const StepParams *prm,
+                        int *err, int grid, cudaStream_t st);
+size_t tc_abuf_bytes(int K, int Q);
 cudaError_t prepare_pipe(int K, int s, int max_smem);
 
 int *tc_error_word(TcWorkspace &ws) {
@@ -677,7 +708,7 @@ void tc_release(TcWorkspace &ws) {
   }
   for (TcWorkspace::Buf *b : {&ws.item0, &ws.seg_count, &ws.seg_base, &ws.pxoff, &ws.scan_blocks,
                               &ws.packed, &ws.xcore, &ws.spill, &ws.r, &ws.badj, &ws.bsyn,
-                              &ws.err}) {
+                              &ws.err, &ws.abuf}) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
     b->bytes = 0;
@@ -790,15 +821,27 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   }));
   if (pipe_ok) TRY(prepare_pipe(K, s, ws.max_smem));
   const int grid2 = std::min(Q, ws.sm_count);
+  // the pipelined synthesis reads every code row as a dense BF16 A tile,
+  // which the pipelined adjoint rewrites after each prox; built here from the
+  // packed warm start (and again whenever the single-stage adjoint, which
+  // does not write it, has run)
+  auto build_abuf = [&]() -> cudaError_t {
+    abuf_kernel<<<Q, kThreads, 0, st>>>(im, Kp, KW, bits, seg_base, pxoff, as<float>(ws.packed),
+                                        as<uint8_t>(ws.abuf));
+    return cudaGetLastError();
+  };
+  if (pipe_ok) {
+    TRY(ensure(ws.abuf, tc_abuf_bytes(K, Q)));
+    TRY(build_abuf());
+  }
 
   // One proximal-gradient iteration with kernel variant v (0 single-stage,
   // 1 pipelined): synthesis, residual, adjoint + prox.
   auto iteration = [&](int v) -> cudaError_t {
     int p1 = ws.prof ? ws.prof->begin(KID_SYNTH_TC, st) : -1;
     if (v == 1) {
-      TRY(launch_syn2(im, K, s, bits, seg_base, pxoff, as<float>(ws.packed), as<uint4>(ws.bsyn),
-                      as<float>(ws.xcore), as<float>(ws.spill), as<int>(ws.err), grid2,
-                      ws.max_smem, st));
+      TRY(launch_syn2(im, K, s, as<uint8_t>(ws.abuf), as<uint4>(ws.bsyn), as<float>(ws.xcore),
+                      as<float>(ws.spill), as<int>(ws.err), grid2, ws.max_smem, st));
     } else {
       TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
         constexpr int S = decltype(SC)::value;
@@ -816,8 +859,9 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
     if (ws.prof) ws.prof->end(p2, st);
     int p3 = ws.prof ? ws.prof->begin(KID_ADJ_TC, st) : -1;
     if (v == 1) {
-      TRY(launch_adj2(im, K, s, bits, seg_base, pxoff, as<float>(ws.packed), as<uint4>(ws.badj),
-                      as<float>(ws.r), prm, as<int>(ws.err), grid2, st));
+      TRY(launch_adj2(im, K, s, bits, seg_base, pxoff, as<float>(ws.packed),
+                      as<uint8_t>(ws.abuf), as<uint4>(ws.badj), as<float>(ws.r), prm,
+                      as<int>(ws.err), grid2, st));
     } else {
       TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
         constexpr int S = decltype(SC)::value;
@@ -854,7 +898,9 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
       float ms[2] = {0.f, 0.f};
       cudaError_t err = cudaSuccess;
       for (int v = 0; v < 2 && err == cudaSuccess; ++v) {
-        err = cudaEventRecord(ev[2 * v], st);
+        // the single-stage adjoint (v = 0) leaves the A tiles behind
+        if (v == 1) err = build_abuf();
+        if (err == cudaSuccess) err = cudaEventRecord(ev[2 * v], st);
         if (err == cudaSuccess) err = iteration(v);
         if (err == cudaSuccess) err = cudaEventRecord(ev[2 * v + 1], st);
       }
@@ -893,6 +939,7 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
     gk.item0 = ws.item0.p;
     gk.off = b.off;
     gk.obs = obs;
+    gk.abuf = ws.abuf.p;
     gk.total_px = b.total_px;
     gk.n_images = b.n;
     gk.K = K;

@@ -163,6 +163,7 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
                                                       const uint64_t *__restrict__ seg_base,
                                                       const uint16_t *__restrict__ pxoff,
                                                       float *__restrict__ packed,
+                                                      uint8_t *__restrict__ abuf,
                                                       const uint4 *__restrict__ badj,
                                                       const float *__restrict__ r,
                                                       const StepParams *__restrict__ prm,
@@ -348,7 +349,9 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
       if (n_items > 1) nxt = next_item(im, cur);
       b2v = seg_base[min(q_begin + 2, Q)];
     }
-    for (int i = 0; i < n_items; ++i) {
+    int staged = n_items > 0 ? 1 : 0;  // items whose staging copy was issued: [0, staged)
+    int i = 0;
+    for (; i < n_items; ++i) {
       const int q = q_begin + i;
       const uint64_t b3v = seg_base[min(q + 3, Q)];
       if (i + 1 < n_items) {
@@ -356,6 +359,7 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
           tc::bulk_wait_read0();  // item i - 1's write-back has left the buffer
           stage_item(b1v, b2v, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
         }
+        staged = i + 2;
         load_masks(nxt, nxt.a, KW, bits, pxoff, px, mwn, pon);
       }
       // this pixel's first value of chunk c_lo inside the staged item
@@ -371,6 +375,8 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
       if (tc::named_sync_or(1, kE, !okw)) break;
       tc::fence_after_sync();
       float *dv = vals(i & 1);
+      // this item's A tile for the next synthesis (dense BF16 codes)
+      uint8_t *const atile = abuf + (size_t)q * kStrip * Kp * 2;
       uint32_t g[32];  // accumulator columns of two chunks (32 filters)
       // running address of the pixel's next sampled value (filter order)
       uint32_t a_run = tc::smem_u32(dv) + 4u * first;
@@ -398,12 +404,25 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
 #pragma unroll
         for (int e2 = 0; e2 < 16; ++e2)
           zv[e2] = tc::ld_shared(ad[e2]);
+        float res[16];
 #pragma unroll
         for (int e2 = 0; e2 < 16; ++e2) {
           const float gv = __uint_as_float(g[(c & 1) * 16 + e2]);
           const float v = zv[e2] - alpha * gv;  // soft threshold as v - clamp(v, -thr, thr)
-          tc::st_shared_if(ad[e2], v - fminf(fmaxf(v, -thr), thr), (mc >> e2) & 1u);
+          res[e2] = v - fminf(fmaxf(v, -thr), thr);
+          tc::st_shared_if(ad[e2], res[e2], (mc >> e2) & 1u);
         }
+        // the pixel's row of the A tile: the new codes in BF16, zero off the
+        // sample (K-major cores of 8 pixels x 8 filters, as the MMA reads them)
+#pragma unroll
+        for (int e2 = 0; e2 < 16; ++e2) res[e2] = ((mc >> e2) & 1u) ? res[e2] : 0.0f;
+        uint8_t *const arow = atile + (size_t)(2 * c) * 2048 + (px >> 3) * 128 + (px & 7) * 16;
+        *reinterpret_cast<uint4 *>(arow) =
+            make_uint4(pack_bf16x2(res[0], res[1]), pack_bf16x2(res[2], res[3]),
+                       pack_bf16x2(res[4], res[5]), pack_bf16x2(res[6], res[7]));
+        *reinterpret_cast<uint4 *>(arow + 2048) =
+            make_uint4(pack_bf16x2(res[8], res[9]), pack_bf16x2(res[10], res[11]),
+                       pack_bf16x2(res[12], res[13]), pack_bf16x2(res[14], res[15]));
       }
       tc::fence_before_sync();
       tc::fence_proxy_async();  // the updated codes, to the bulk copy below
@@ -424,7 +443,13 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
       b2v = b3v;
       if (i + 2 < n_items) nxt = next_item(im, nxt);
     }
-    if (e == 0) tc::bulk_wait0();  // write-backs complete before the CTA exits
+    if (e == 0) {
+      // staging copies issued but not consumed (after an abort) land, and the
+      // write-backs complete, before the CTA exits
+      for (int j = i; j < staged; ++j)
+        tc::mbar_wait_bounded(&stg_full[j & 1], (uint32_t)((j >> 1) & 1), kWaitNs);
+      tc::bulk_wait0();
+    }
   }
 
   __syncthreads();
@@ -438,27 +463,24 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
 
 // ================================================================== synthesis
 
+constexpr int kMaxAb = 4;  // A-operand buffers of the synthesis, at most
+
 template <int S>
 struct Syn2 {
   static constexpr int C = (S - 1) / 2;
   static constexpr int N = 16 * S;
+  static constexpr int kThreads = 160;  // warps 0-3 fold and issue, warp 4 copies
   __host__ __device__ static size_t a_bytes(int Kp) { return (size_t)kStrip * Kp * 2; }
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)N * Kp * 2; }
-  __host__ __device__ static size_t vals_bytes(int Kp) { return (size_t)kStrip * Kp * 4; }
-  __host__ __device__ static size_t mask_bytes(int KW) { return (size_t)kStrip * KW * 4; }
-  // nst staging buffers of packed codes, nab A-operand buffers
-  __host__ __device__ static size_t total(int Kp, int KW, int nst, int nab) {
-    return 1024 + (size_t)nab * a_bytes(Kp) + b_bytes(Kp) + (size_t)nst * vals_bytes(Kp) +
-           (size_t)2 * 4 * 2 * S * S * 4;
+  // nab A-operand buffers (dense BF16 code tiles, filled by bulk copies)
+  __host__ __device__ static size_t total(int Kp, int nab) {
+    return 1024 + (size_t)nab * a_bytes(Kp) + b_bytes(Kp) + (size_t)2 * 4 * 2 * S * S * 4;
   }
-  // the largest buffering that fits: (2, 2), else (2, 1), else (1, 1)
-  static void pick(int Kp, int KW, int max_smem, int &nst, int &nab) {
-    nst = 2;
-    nab = 2;
-    if (total(Kp, KW, nst, nab) <= (size_t)max_smem) return;
-    nab = 1;
-    if (total(Kp, KW, nst, nab) <= (size_t)max_smem) return;
-    nst = 1;
+  // as many A buffers as fit, up to kMaxAb (0 if not even one fits)
+  static int pick(int Kp, int max_smem) {
+    int nab = kMaxAb;
+    while (nab > 0 && total(Kp, nab) > (size_t)max_smem) --nab;
+    return nab;
   }
 };
 
@@ -490,35 +512,21 @@ struct CodeRowGen {
 };
 
 template <int S>
-__global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp, int KW, int nst,
-                                                      int nab,
-                                                      const uint32_t *__restrict__ bits,
-                                                      const uint64_t *__restrict__ seg_base,
-                                                      const uint16_t *__restrict__ pxoff,
-                                                      const float *__restrict__ packed,
-                                                      const uint4 *__restrict__ bsyn,
-                                                      float *__restrict__ xcore,
-                                                      float *__restrict__ spill, int *err) {
+__global__ void __launch_bounds__(Syn2<S>::kThreads, 1) syn2_kernel(
+    ItemMap im, int K, int Kp, int nab, const uint8_t *__restrict__ abuf,
+    const uint4 *__restrict__ bsyn, float *__restrict__ xcore, float *__restrict__ spill,
+    int *err) {
   using L = Syn2<S>;
   constexpr int C = L::C, N = L::N;
   const int NC = Kp / 16;
+  const uint32_t tile_bytes = (uint32_t)L::a_bytes(Kp);
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = align1024(smem_raw);
-  uint8_t *const As0 = smem;
-  uint8_t *const As1 = As0 + (nab == 2 ? L::a_bytes(Kp) : 0);
-  uint8_t *Bs = As1 + L::a_bytes(Kp);
-  uint8_t *p = Bs + L::b_bytes(Kp);
-  float *const vals0 = reinterpret_cast<float *>(p);
-  p += L::vals_bytes(Kp);
-  float *vals1 = vals0;
-  if (nst == 2) {
-    vals1 = reinterpret_cast<float *>(p);
-    p += L::vals_bytes(Kp);
-  }
-  auto vals = [&](int k) { return (k & 1) ? vals1 : vals0; };
-  float *Pu = reinterpret_cast<float *>(p);  // edge exchange of the col2im, [2][4][2c][S]
+  uint8_t *const As = smem;  // nab A tiles
+  uint8_t *Bs = As + (size_t)nab * tile_bytes;
+  float *Pu = reinterpret_cast<float *>(Bs + L::b_bytes(Kp));  // col2im edge exchange [2][4][2c][S]
 
-  __shared__ uint64_t tfull[2], stg_full[2], a_full[2], a_free[2], done_bar;
+  __shared__ uint64_t tfull[2], a_full[kMaxAb], a_free[kMaxAb], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
@@ -528,11 +536,10 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) {
-      tc::mbar_init(&tfull[i], 1);
-      tc::mbar_init(&stg_full[i], 1);
-      tc::mbar_init(&a_full[i], 4);  // one arrival per expanding warp
-      tc::mbar_init(&a_free[i], 1);
+    for (int i = 0; i < 2; ++i) tc::mbar_init(&tfull[i], 1);
+    for (int i = 0; i < kMaxAb; ++i) {
+      tc::mbar_init(&a_full[i], 1);  // the copy's expect-tx arrival
+      tc::mbar_init(&a_free[i], 1);  // the MMA commit
     }
     tc::mbar_init(&done_bar, 1);
     abort_flag = 0;
@@ -554,106 +561,30 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
   const int q_end = (int)((int64_t)Q * (blockIdx.x + 1) / gridDim.x);
   volatile int *abort_v = &abort_flag;
 
-  auto a_buf = [&](int r) { return (nab == 2 && (r & 1)) ? As1 : As0; };
-  if (warp < 4) {
-    // ------------------------------------------------ expand
-    // Each warp runs on its own mbarrier waits (lane 0 waits, the warp
-    // follows) and signals a_full when its 32 pixels of the row are in A.
-    const int e = tid;
-    // code rows in sequence: g (current), nx (next), nn (after next); the
-    // seg_base values of each row are loaded one iteration before they are used
-    auto base_of = [&](int qq) { return seg_base[qq]; };
-    CodeRowGen g;
-    g.init(q_begin, q_end, C);
-    bool have = g.next(im);
-    CodeRowGen nx = g;
-    bool have_nx = have && nx.next(im);
-    uint64_t nb0 = 0, nb1 = 0;
-    if (have_nx) {
-      nb0 = base_of(nx.q());
-      nb1 = base_of(nx.q() + 1);
-    }
-    // staged codes: one bulk copy per code row into vals(row parity) (or the
-    // single buffer); mask words: registers, loaded one row ahead
-    uint32_t mw[4], mwn[4], po = 0, pon = 0;
-    if (have) {
-      if (e == 0) stage_item(base_of(g.q()), base_of(g.q() + 1), packed, vals(0), &stg_full[0]);
-      load_masks(g.sg.it, g.a, KW, bits, pxoff, e, mw, po);
-    }
-    int i = 0;
-    while (have) {
-      CodeRowGen nn = nx;
-      const bool have_nn = have_nx && nn.next(im);
-      uint64_t mb0 = 0, mb1 = 0;
-      if (have_nn) {
-        mb0 = base_of(nn.q());
-        mb1 = base_of(nn.q() + 1);
+  auto a_buf = [&](int r) { return As + (size_t)(r % nab) * tile_bytes; };
+  if (warp == 4) {
+    // ------------------------------------------------ A tiles
+    // Code row r's dense BF16 codes (written by the adjoint's epilogue in
+    // the A-operand layout) arrive by one bulk copy into buffer r % nab,
+    // once the MMAs of row r - nab have released it.
+    if (lane == 0) {
+      CodeRowGen g;
+      g.init(q_begin, q_end, C);
+      int i = 0;
+      while (g.next(im)) {
+        const int ab = i % nab;
+        if (i >= nab &&
+            !tc::mbar_wait_abortable(&a_free[ab], (uint32_t)(((i - nab) / nab) & 1), abort_v,
+                                     kWaitNs))
+          break;
+        tc::mbar_arrive_expect_tx(&a_full[ab], tile_bytes);
+        tc::bulk_g2s(a_buf(i), abuf + (size_t)g.q() * tile_bytes, tile_bytes, &a_full[ab]);
+        ++i;
       }
-      const int sb = nst == 2 ? (i & 1) : 0;
-      const int ab = nab == 2 ? (i & 1) : 0;
-      bool w = true;
-      if (have_nx) {
-        // two staging buffers: row i + 1 replaces row i - 1 once all four
-        // warps have expanded it
-        if (nst == 2 && e == 0) {
-          if (i >= 1) {
-            const int pb = nab == 2 ? ((i - 1) & 1) : 0;
-            w = tc::mbar_wait_abortable(&a_full[pb], (uint32_t)(((i - 1) / nab) & 1), abort_v,
-                                        kWaitNs);
-          }
-          if (w) stage_item(nb0, nb1, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
-        }
-        load_masks(nx.sg.it, nx.a, KW, bits, pxoff, e, mwn, pon);
-      }
-      if (lane == 0 && w) {
-        w = tc::mbar_wait_abortable(&stg_full[sb], (uint32_t)((nst == 2 ? (i >> 1) : i) & 1),
-                                    abort_v, kWaitNs);
-        if (w && i >= nab)
-          w = tc::mbar_wait_abortable(&a_free[ab], (uint32_t)(((i - nab) / nab) & 1), abort_v,
-                                      kWaitNs);
-      }
-      if (!__shfl_sync(0xffffffffu, w, 0)) break;
-      const float *dv = vals(sb);
-      uint8_t *const As = a_buf(i);
-      // running address of the pixel's next sampled value (filter order)
-      uint32_t a_run = tc::smem_u32(dv) + 4u * po;
-#pragma unroll
-      for (int c = 0; c < kMaxNC; ++c) {
-        if (c >= NC) break;
-        const uint32_t mc = chunk_bits(mw, c);
-        float v[16];
-#pragma unroll
-        for (int e2 = 0; e2 < 16; ++e2) {
-          const float t = tc::ld_shared(a_run);
-          v[e2] = ((mc >> e2) & 1u) ? t : 0.0f;
-          a_run += ((mc >> e2) & 1u) << 2;
-        }
-        uint4 lo = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
-                              pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-        uint4 hi = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
-                              pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
-        uint8_t *dst = As + (size_t)(2 * c) * 2048 + (e >> 3) * 128 + (e & 7) * 16;
-        *reinterpret_cast<uint4 *>(dst) = lo;
-        *reinterpret_cast<uint4 *>(dst + 2048) = hi;
-      }
-      tc::fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&a_full[ab]);
-      if (nst == 1 && have_nx && e == 0) {
-        // one staging buffer: row i + 1 replaces row i once it is expanded
-        if (tc::mbar_wait_abortable(&a_full[ab], (uint32_t)((i / nab) & 1), abort_v, kWaitNs))
-          stage_item(nb0, nb1, packed, vals(0), &stg_full[0]);
-      }
-#pragma unroll
-      for (int w2 = 0; w2 < 4; ++w2) mw[w2] = mwn[w2];
-      po = pon;
-      g = nx;
-      have = have_nx;
-      nx = nn;
-      have_nx = have_nn;
-      nb0 = mb0;
-      nb1 = mb1;
-      ++i;
+      // the last copies have landed before the CTA may exit (they are
+      // normally consumed already; this matters after an abort)
+      for (int r = i > nab ? i - nab : 0; r < i; ++r)
+        tc::mbar_wait_bounded(&a_full[r % nab], (uint32_t)((r / nab) & 1), kWaitNs);
     }
   } else {
     // ------------------------------------------------ epilogue: col2im
@@ -664,7 +595,7 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     // it is < 0): those land on the c right-edge and c left-edge lanes, are
     // exchanged once per code row, and at the strip's outer edges accumulate
     // the spill columns.
-    const int e = tid - 128, ew = e >> 5;
+    const int e = tid, ew = e >> 5;
     const uint32_t lane_base = taddr + ((uint32_t)(32 * ew) << 16);
     const bool left_edge = lane < C, right_edge = lane >= 32 - C;
     // taps v whose source lane L + c - v lies inside the warp (bit v)
@@ -677,14 +608,14 @@ __global__ void __launch_bounds__(256, 1) syn2_kernel(ItemMap im, int K, int Kp,
     const bool spill_lane = (ew == 0 && right_edge) || (ew == 3 && left_edge);
     const int spill_slot = ew == 0 ? lane - (32 - C) : C + lane;
     // MMA issue (thread e = 0), one code row ahead of the col2im: P = Z D^T of
-    // row r into TMEM buffer r & 1 once the four expanding warps are done.
+    // row r into TMEM buffer r & 1 once its A tile has landed.
     // The buffer's previous row was folded by this group before the group
     // barrier that precedes the issue, so no TMEM-empty barrier is needed.
     const uint32_t idesc = tc::idesc_bf16_f32(128, N);
     const uint32_t b_base = tc::smem_u32(Bs);
     const uint32_t b_lbo = 2 * S * 128;
     auto issue = [&](int r) -> bool {
-      const int ab = nab == 2 ? (r & 1) : 0;
+      const int ab = r % nab;
       if (!tc::mbar_wait_abortable(&a_full[ab], (uint32_t)((r / nab) & 1), abort_v, kWaitNs))
         return false;
       tc::fence_after_sync();
@@ -844,55 +775,52 @@ bool tc_pipe_supported(int K, int s, int max_smem) {
   dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
     need = Adj2<S>::total(Kp, KW);
-    size_t syn = Syn2<S>::total(Kp, KW, 1, 1);
+    size_t syn = Syn2<S>::total(Kp, 1);
     if (syn > need) need = syn;
     return cudaSuccess;
   });
   return need > 0 && need <= (size_t)max_smem;
 }
 
-// Shared-memory attributes of both pipelined kernels (set once, outside any
-// stream capture).
 cudaError_t prepare_pipe(int K, int s, int max_smem) {
   const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
   return dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
-    int nst, nab;
-    Syn2<S>::pick(Kp, KW, max_smem, nst, nab);
+    const int nab = Syn2<S>::pick(Kp, max_smem);
     cudaError_t e = cudaFuncSetAttribute(syn2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Syn2<S>::total(Kp, KW, nst, nab));
+                                         (int)Syn2<S>::total(Kp, nab));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(adj2_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Adj2<S>::total(Kp, KW));
   });
 }
 
-cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
-                        const uint64_t *seg_base, const uint16_t *pxoff, const float *packed,
+size_t tc_abuf_bytes(int K, int Q) { return (size_t)Q * kStrip * ((K + 15) / 16 * 16) * 2; }
+
+cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint8_t *abuf,
                         const uint4 *bsyn, float *xcore, float *spill, int *err, int grid,
                         int max_smem, cudaStream_t st) {
-  const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
+  const int Kp = (K + 15) / 16 * 16;
   return dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
-    int nst, nab;
-    Syn2<S>::pick(Kp, KW, max_smem, nst, nab);
-    const size_t smem = Syn2<S>::total(Kp, KW, nst, nab);
-    syn2_kernel<S><<<grid, 256, smem, st>>>(im, K, Kp, KW, nst, nab, bits, seg_base, pxoff,
-                                            packed, bsyn, xcore, spill, err);
+    const int nab = Syn2<S>::pick(Kp, max_smem);
+    const size_t smem = Syn2<S>::total(Kp, nab);
+    syn2_kernel<S><<<grid, Syn2<S>::kThreads, smem, st>>>(im, K, Kp, nab, abuf, bsyn, xcore,
+                                                          spill, err);
     return cudaGetLastError();
   });
 }
 
 cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
                         const uint64_t *seg_base, const uint16_t *pxoff, float *packed,
-                        const uint4 *badj, const float *r, const StepParams *prm, int *err,
-                        int grid, cudaStream_t st) {
+                        uint8_t *abuf, const uint4 *badj, const float *r, const StepParams *prm,
+                        int *err, int grid, cudaStream_t st) {
   const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
   return dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
     const size_t smem = Adj2<S>::total(Kp, KW);
     adj2_kernel<S><<<grid, Adj2<S>::kThreads, smem, st>>>(im, K, Kp, KW, bits, seg_base, pxoff,
-                                                          packed, badj, r, prm, err);
+                                                          packed, abuf, badj, r, prm, err);
     return cudaGetLastError();
   });
 }

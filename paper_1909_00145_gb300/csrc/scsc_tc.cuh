@@ -24,7 +24,7 @@ struct TuneKey {
 // the by-value launch arguments that follow from the batch shape).
 struct GraphKey {
   const void *bits, *seg_base, *pxoff, *packed, *bsyn, *badj, *xcore, *spill, *r, *err, *x, *prm,
-      *item0, *off, *obs;
+      *item0, *off, *obs, *abuf;
   int64_t total_px;
   int n_images, K, s, Q, variant, iters;
 };
@@ -45,6 +45,7 @@ struct TcWorkspace {
     size_t bytes = 0;
   };
   Buf item0, seg_count, seg_base, pxoff, scan_blocks, packed, xcore, spill, r, badj, bsyn, err;
+  Buf abuf;  // dense BF16 code tiles in the synthesis A-operand layout (pipelined kernels)
   std::vector<int> host_item0;  // cached row-item map of the last batch
   std::vector<int> host_H, host_W;
   int n_items = 0;
