@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(Syn2<S>::kThreads, 1) syn2_kernel(
   uint8_t *Bs = As + (size_t)nab * tile_bytes;
   float *Pu = reinterpret_cast<float *>(Bs + L::b_bytes(Kp));  // col2im edge exchange [2][4][2c][S]
 
-  __shared__ uint64_t tfull[2], a_full[kMaxAb], a_free[kMaxAb], done_bar;
+  __shared__ uint64_t tfull[2], tempty[2], a_full[kMaxAb], a_free[kMaxAb], done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
 
@@ -536,7 +536,10 @@ __global__ void __launch_bounds__(Syn2<S>::kThreads, 1) syn2_kernel(
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    for (int i = 0; i < 2; ++i) tc::mbar_init(&tfull[i], 1);
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&tfull[i], 1);
+      tc::mbar_init(&tempty[i], 4);  // one arrival per folding warp
+    }
     for (int i = 0; i < kMaxAb; ++i) {
       tc::mbar_init(&a_full[i], 1);  // the copy's expect-tx arrival
       tc::mbar_init(&a_free[i], 1);  // the MMA commit
@@ -563,28 +566,59 @@ __global__ void __launch_bounds__(Syn2<S>::kThreads, 1) syn2_kernel(
 
   auto a_buf = [&](int r) { return As + (size_t)(r % nab) * tile_bytes; };
   if (warp == 4) {
-    // ------------------------------------------------ A tiles
+    // ------------------------------------------------ A tiles and MMA issue
     // Code row r's dense BF16 codes (written by the adjoint's epilogue in
-    // the A-operand layout) arrive by one bulk copy into buffer r % nab,
-    // once the MMAs of row r - nab have released it.
+    // the A-operand layout) arrive by one bulk copy into buffer r % nab, up
+    // to nab rows ahead, once the MMAs of row r - nab have released it; then
+    // P = Z D^T of row r goes into TMEM buffer r & 1 once the folding group
+    // has emptied it (row r - 2).
     if (lane == 0) {
-      CodeRowGen g;
+      const uint32_t idesc = tc::idesc_bf16_f32(128, N);
+      const uint32_t b_base = tc::smem_u32(Bs);
+      const uint32_t b_lbo = 2 * S * 128;
+      CodeRowGen g;  // the next row to copy
       g.init(q_begin, q_end, C);
-      int i = 0;
-      while (g.next(im)) {
-        const int ab = i % nab;
-        if (i >= nab &&
-            !tc::mbar_wait_abortable(&a_free[ab], (uint32_t)(((i - nab) / nab) & 1), abort_v,
-                                     kWaitNs))
-          break;
-        tc::mbar_arrive_expect_tx(&a_full[ab], tile_bytes);
-        tc::bulk_g2s(a_buf(i), abuf + (size_t)g.q() * tile_bytes, tile_bytes, &a_full[ab]);
-        ++i;
+      bool more = g.next(im);
+      int copied = 0;
+      bool ok = true;
+      for (int r = 0; ok; ++r) {
+        while (more && copied < r + nab) {
+          const int ab = copied % nab;
+          if (copied >= nab &&
+              !tc::mbar_wait_abortable(&a_free[ab], (uint32_t)(((copied - nab) / nab) & 1),
+                                       abort_v, kWaitNs)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_arrive_expect_tx(&a_full[ab], tile_bytes);
+          tc::bulk_g2s(a_buf(copied), abuf + (size_t)g.q() * tile_bytes, tile_bytes,
+                       &a_full[ab]);
+          ++copied;
+          more = g.next(im);
+        }
+        if (!ok || r >= copied) break;  // every row copied has been multiplied
+        const int ab = r % nab, b = r & 1;
+        ok = tc::mbar_wait_abortable(&a_full[ab], (uint32_t)((r / nab) & 1), abort_v, kWaitNs) &&
+             tc::mbar_wait_abortable(&tempty[b], (uint32_t)(((r >> 1) & 1) ^ 1), abort_v,
+                                     kWaitNs);
+        if (!ok) break;
+        tc::fence_after_sync();
+        const uint32_t a_base = tc::smem_u32(a_buf(r));
+#pragma unroll 1
+        for (int kk = 0; kk < NC; ++kk) {
+          uint64_t ad = tc::smem_desc(a_base + kk * 2 * 2048, 2048, 128);
+          uint64_t bd = tc::smem_desc(b_base + kk * 2 * b_lbo, b_lbo, 128);
+          tc::mma_bf16(taddr + b * 256, ad, bd, idesc, kk > 0 ? 1u : 0u);
+        }
+        tc::mma_commit(&tfull[b]);
+        tc::mma_commit(&a_free[ab]);
       }
-      // the last copies have landed before the CTA may exit (they are
-      // normally consumed already; this matters after an abort)
-      for (int r = i > nab ? i - nab : 0; r < i; ++r)
+      // the last copies have landed and the MMAs issued are complete before
+      // the CTA may exit (normally already so; this matters after an abort)
+      for (int r = copied > nab ? copied - nab : 0; r < copied; ++r)
         tc::mbar_wait_bounded(&a_full[r % nab], (uint32_t)((r / nab) & 1), kWaitNs);
+      tc::mma_commit(&done_bar);
+      tc::mbar_wait_bounded(&done_bar, 0, kWaitNs);
     }
   } else {
     // ------------------------------------------------ epilogue: col2im
@@ -607,37 +641,7 @@ __global__ void __launch_bounds__(Syn2<S>::kThreads, 1) syn2_kernel(
     // c + j = column b0 + 128 + j (warp 3, lane j)
     const bool spill_lane = (ew == 0 && right_edge) || (ew == 3 && left_edge);
     const int spill_slot = ew == 0 ? lane - (32 - C) : C + lane;
-    // MMA issue (thread e = 0), one code row ahead of the col2im: P = Z D^T of
-    // row r into TMEM buffer r & 1 once its A tile has landed.
-    // The buffer's previous row was folded by this group before the group
-    // barrier that precedes the issue, so no TMEM-empty barrier is needed.
-    const uint32_t idesc = tc::idesc_bf16_f32(128, N);
-    const uint32_t b_base = tc::smem_u32(Bs);
-    const uint32_t b_lbo = 2 * S * 128;
-    auto issue = [&](int r) -> bool {
-      const int ab = r % nab;
-      if (!tc::mbar_wait_abortable(&a_full[ab], (uint32_t)((r / nab) & 1), abort_v, kWaitNs))
-        return false;
-      tc::fence_after_sync();
-      const uint32_t a_base = tc::smem_u32(a_buf(r));
-#pragma unroll 1
-      for (int kk = 0; kk < NC; ++kk) {
-        uint64_t ad = tc::smem_desc(a_base + kk * 2 * 2048, 2048, 128);
-        uint64_t bd = tc::smem_desc(b_base + kk * 2 * b_lbo, b_lbo, 128);
-        tc::mma_bf16(taddr + (r & 1) * 256, ad, bd, idesc, kk > 0 ? 1u : 0u);
-      }
-      tc::mma_commit(&tfull[r & 1]);
-      tc::mma_commit(&a_free[ab]);
-      return true;
-    };
-    int n_rows = 0;  // code rows of this CTA
-    {
-      SegIter cnt{q_begin, q_end};
-      while (cnt.next(im)) n_rows += min(cnt.it.H, cnt.o1 + C) - max(0, cnt.o0 - C);
-    }
     bool ok = true;
-    if (e == 0 && n_rows > 0) ok = issue(0);
-    ok = !tc::named_sync_or(2, 128, !ok);  // the group leaves together on a failed wait
     SegIter sg{q_begin, q_end};
     int i = 0;
     while (ok && sg.next(im)) {
@@ -649,12 +653,9 @@ __global__ void __launch_bounds__(Syn2<S>::kThreads, 1) syn2_kernel(
       for (int u = 0; u < S; ++u) acc[u] = acch[u] = 0.0f;
       for (int a = a_start; a < a_end; ++a, ++i) {
         const int b = i & 1;
-        bool okw = ok;
-        if (e == 0) {
-          if (okw && i + 1 < n_rows) okw = issue(i + 1);
-          if (okw)
-            okw = tc::mbar_wait_abortable(&tfull[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
-        }
+        bool okw = true;
+        if (e == 0)
+          okw = tc::mbar_wait_abortable(&tfull[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
         if (tc::named_sync_or(2, 128, !okw)) {
           ok = false;
           break;
@@ -688,10 +689,11 @@ __global__ void __launch_bounds__(Syn2<S>::kThreads, 1) syn2_kernel(
           acc[u] += own0 + own1;
           hacc[u] = hal;
         }
-        // TMEM reads of this row end before the group barrier below, after
-        // which thread 0 may overwrite the buffer (row i + 2)
+        // TMEM reads of this row are done: the MMA thread may refill the
+        // buffer (row i + 2)
         tc::fence_before_sync();
-        if (C == 0) tc::named_sync(2, 128);
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&tempty[b]);
         if (C > 0) {
           // edge partial sums of warp ew: slot j < c = its left neighbour's
           // column 32 - c + j (lane 32 - c + j), slot c + j = its right
@@ -737,10 +739,6 @@ __global__ void __launch_bounds__(Syn2<S>::kThreads, 1) syn2_kernel(
           if (spill_lane) spill[(int64_t)(it.q_row0 + o) * (2 * C) + spill_slot] = acch[j];
         }
       }
-    }
-    if (e == 0) {  // the MMAs issued are complete before the TMEM is released
-      tc::mma_commit(&done_bar);
-      tc::mbar_wait_bounded(&done_bar, 0, kWaitNs);
     }
   }
 
