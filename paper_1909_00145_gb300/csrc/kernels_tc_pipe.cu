@@ -8,15 +8,15 @@
 // groups of four warps (each covers all 128 pixels of the item and half of its
 // filter chunks): they prefetch the next item's packed codes with one bulk
 // copy and its mask words and pixel offsets into registers, apply the
-// soft-threshold step to the sampled coordinates and write the item back with
-// one bulk copy.
+// soft-threshold step to the sampled coordinates, write the item back with
+// one bulk copy, and write the item's dense BF16 codes (zero off the sample)
+// in the synthesis's A-operand layout.
 //
-// Synthesis, 8 warps: warps 0-3 expand the staged packed codes of a code row
-// into the BF16 A operand (two buffers when shared memory allows); warps 4-7
-// fold P = Z D^T into output rows (col2im by warp shuffles, the warp-edge halo
-// exchanged through shared memory) and write the strip's core columns and its
-// 2c spill columns; their first thread issues the MMAs of the next code row
-// into the other of two TMEM accumulators before folding the current one.
+// Synthesis, 5 warps: warp 4 (lane 0) fetches each code row's dense BF16 A
+// tile by one bulk copy (up to 4 rows ahead) and issues the MMAs P = Z D^T
+// into one of two TMEM accumulators; warps 0-3 fold P into output rows
+// (col2im by warp shuffles, the warp-edge halo exchanged through shared
+// memory) and write the strip's core columns and its 2c spill columns.
 //
 // Every wait is bounded; on timeout the CTA raises an abort flag, all roles
 // leave their loops, the MMAs already issued are waited for (bounded) and the
