@@ -3,7 +3,9 @@
 TEST INFRASTRUCTURE ONLY.  This package is the plain, slow statement of what
 the GPU library computes: the CSC objective (Eq. 1), the subsampled code
 problem (Eq. 3) solved by proximal gradient, the up-projection (Eq. 4), the
-batch dictionary step (Eq. 5) and the online surrogates (Eq. 7, Eq. 8) of
+batch dictionary step (Eq. 5), the online surrogates (Eq. 7, Eq. 8), the
+ADMM and Gauss-Seidel solvers (Sec. 3.2), inpainting (Sec. 4.3) and safe
+screening of the code problem (Sec. 5) of
 Xiong, Richtarik & Heidrich, "Stochastic Convolutional Sparse Coding" (2019).
 Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import it; the product path never does.
@@ -72,6 +74,9 @@ def lib() -> ctypes.CDLL:
                 "orc_power_dense": (dbl, [i, P, u64, u64, i]),
                 "orc_surrogate_accumulate": (None, [i, i, i, i, P, P, dbl, P, P]),
                 "orc_admm_image": (None, [i, i, i, i, P, P, P, P, dbl, dbl, dbl, i, i]),
+                "orc_screen_image": (ctypes.c_int64, [i, i, i, i, P, P, P, P, dbl, P, P]),
+                "orc_code_update_image_screened": (ctypes.c_int64, [i, i, i, i, P, P, P, P, dbl,
+                                                                    dbl, i, i, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)

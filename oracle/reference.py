@@ -333,3 +333,47 @@ def admm_image(cfg: Config, d, x, z, mask, H: int, W: int, n_iters: int,
     lib().orc_admm_image(cfg.K, cfg.s, H, W, _p(d), _p(x), _p(z), _p(m), cfg.lam, rho,
                          alpha_r, n_iters, cg_iters)
     return z
+
+
+def screen_image(cfg: Config, d, x, z, mask, H: int, W: int):
+    """Duality-gap sphere test on Eq. 3 for one image (Sec. 5: safe screening
+    of the code LASSO).  Returns (z, mask, gap, stat): the codes and active
+    set with the coordinates proven zero removed, the duality gap at the
+    input codes, and the per-coordinate statistic (NaN off the input set)."""
+    d, x = _f64(d), _f64(x)
+    z = _f64(z).copy()
+    m = np.ascontiguousarray(mask, dtype=np.uint8).ravel().copy()
+    stat = np.empty(H * W * cfg.K)
+    gap = ctypes.c_double(0.0)
+    lib().orc_screen_image(cfg.K, cfg.s, H, W, _p(d), _p(x), _p(z), _p(m), cfg.lam,
+                           ctypes.byref(gap), _p(stat))
+    return z, m, float(gap.value), stat
+
+
+def code_step_screened(cfg: Config, batch: Batch, x, d, z, t: int, n_iters: int,
+                       screen_every: int, step: float | None = None):
+    """code_step with the screening test run on each image's active set before
+    iterations 0, e, 2e, ... (e = screen_every; 0 = never).  Returns (z,
+    active mask [sum_n H_n W_n K], per-image gap of the last test)."""
+    x, d = _f64(x), _f64(d)
+    z = _f64(z).copy()
+    if step is None:
+        L = lipschitz_codes(cfg, d, int(batch.H.max()), int(batch.W.max()))
+        alpha = 1.0 / L if L > 0 else 0.0
+    else:
+        alpha = float(step)
+    masks, gaps = [], []
+    for n in range(batch.n):
+        H, W = int(batch.H[n]), int(batch.W[n])
+        m = np.ascontiguousarray(mask_image(cfg, t, int(batch.ids[n]), H, W).ravel())
+        zi = np.ascontiguousarray(batch.image(z, n, cfg.K))
+        xi = np.ascontiguousarray(batch.image(x, n))
+        gap = ctypes.c_double(0.0)
+        lib().orc_code_update_image_screened(cfg.K, cfg.s, H, W, _p(d), _p(xi), _p(zi), _p(m),
+                                             alpha, cfg.lam, n_iters, screen_every,
+                                             ctypes.byref(gap))
+        o = int(batch.off[n]) * cfg.K
+        z[o:o + zi.size] = zi
+        masks.append(m)
+        gaps.append(float(gap.value))
+    return z, np.concatenate(masks) if masks else np.zeros(0, np.uint8), np.array(gaps)

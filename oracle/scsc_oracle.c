@@ -421,3 +421,104 @@ void orc_admm_image(int K, int s, int H, int W, const double *d,
   free(y); free(u); free(b); free(atx); free(res); free(p); free(Ap);
   free(q.pix); free(q.tmp);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Safe screening of the code problem (Sec. 5)                               */
+/* ------------------------------------------------------------------------ */
+
+/* Margins of the sphere test (see scsc_oracle.h). */
+#define SCREEN_ETA 1e-6
+#define SCREEN_TAU 1e-4
+
+/* ||a_j||^2 for column j = (k, a, b) of D: code z_k(a, b) reaches pixel
+ * (a - c + u, b - c + v) with weight d_k(u, v); taps off the image drop. */
+static double column_norm2(int s, int H, int W, const double *d, int k, int a,
+                           int b) {
+  const int c = (s - 1) / 2;
+  double acc = 0.0;
+  for (int u = 0; u < s; ++u)
+    for (int v = 0; v < s; ++v) {
+      int i = a - c + u, j = b - c + v;
+      if (i < 0 || i >= H || j < 0 || j >= W) continue;
+      double w = d[((size_t)k * s + u) * s + v];
+      acc += w * w;
+    }
+  return acc;
+}
+
+int64_t orc_screen_image(int K, int s, int H, int W, const double *d,
+                         const double *x, double *z, uint8_t *mask,
+                         double lambda, double *gap_out, double *stat) {
+  size_t D = (size_t)H * W, DK = D * (size_t)K;
+  double *rho = (double *)malloc(D * sizeof(double));
+  double *corr = (double *)malloc(DK * sizeof(double));
+  for (size_t i = 0; i < DK; ++i)
+    if (!mask[i]) z[i] = 0.0;
+  /* residual rho = x - D z and correlations a_j . rho = (D^T rho)_j */
+  orc_synthesis(K, s, H, W, d, z, rho);
+  for (size_t i = 0; i < D; ++i) rho[i] = x[i] - rho[i];
+  orc_adjoint(K, s, H, W, d, rho, corr);
+  double scale = lambda, l1 = 0.0;
+  for (size_t i = 0; i < DK; ++i)
+    if (mask[i]) {
+      if (fabs(corr[i]) > scale) scale = fabs(corr[i]);
+      l1 += fabs(z[i]);
+    }
+  /* primal value, dual value at theta = rho / scale, their gap */
+  double data = 0.0, dist = 0.0, xx = 0.0;
+  for (size_t i = 0; i < D; ++i) {
+    double theta = rho[i] / scale, e = theta - x[i] / lambda;
+    data += rho[i] * rho[i];
+    dist += e * e;
+    xx += x[i] * x[i];
+  }
+  double primal = 0.5 * data + lambda * l1;
+  double dual = 0.5 * xx - 0.5 * lambda * lambda * dist;
+  double gap = primal - dual;
+  if (gap < 0.0) gap = 0.0;
+  /* the sphere uses the gap plus SCREEN_ETA (P + ||x||^2 / 2): a bound on the
+   * rounding of P and the dual value in FP32 sums of that magnitude */
+  double radius = sqrt(2.0 * (gap + SCREEN_ETA * (primal + 0.5 * xx))) / lambda;
+  int64_t kept = 0;
+  for (int a = 0; a < H; ++a)
+    for (int b = 0; b < W; ++b)
+      for (int k = 0; k < K; ++k) {
+        size_t i = ((size_t)a * W + b) * K + k;
+        if (!mask[i]) {
+          if (stat) stat[i] = NAN;
+          continue;
+        }
+        double t = fabs(corr[i]) / scale +
+                   radius * sqrt(column_norm2(s, H, W, d, k, a, b));
+        if (stat) stat[i] = t;
+        if (t < 1.0 - SCREEN_TAU) {
+          mask[i] = 0;
+          z[i] = 0.0;
+        } else {
+          ++kept;
+        }
+      }
+  if (gap_out) *gap_out = gap;
+  free(rho);
+  free(corr);
+  return kept;
+}
+
+int64_t orc_code_update_image_screened(int K, int s, int H, int W,
+                                       const double *d, const double *x,
+                                       double *z, uint8_t *mask, double alpha,
+                                       double lambda, int n_iters,
+                                       int screen_every, double *gap_out) {
+  size_t DK = (size_t)H * W * K;
+  int64_t kept = 0;
+  for (size_t i = 0; i < DK; ++i) {
+    if (!mask[i]) z[i] = 0.0;
+    kept += mask[i] != 0;
+  }
+  for (int it = 0; it < n_iters; ++it) {
+    if (screen_every > 0 && it % screen_every == 0)
+      kept = orc_screen_image(K, s, H, W, d, x, z, mask, lambda, gap_out, NULL);
+    orc_code_update_image(K, s, H, W, d, x, z, mask, alpha, lambda, 1);
+  }
+  return kept;
+}

@@ -113,6 +113,38 @@ void orc_admm_image(int K, int s, int H, int W, const double *d,
                     double lambda, double rho, double alpha_r, int n_iters,
                     int cg_iters);
 
+/* Safe screening of the code problem (Sec. 5 names safe screening of this
+ * sparse LASSO as a way to skip updates; the rule below is the duality-gap
+ * sphere test).  Problem: Eq. 3 for one image restricted to the active set
+ * S = {mask != 0}: P(z) = 0.5 ||x - D z||^2 + lambda ||z_S||_1.  Its dual is
+ *   Dual(theta) = 0.5 ||x||^2 - 0.5 lambda^2 || theta - x / lambda ||^2
+ *   over |a_j . theta| <= 1 for j in S  (a_j = column j of D).
+ * At the current z (set to zero off S first): rho = x - D z, the dual point
+ * theta = rho / max(lambda, max_{j in S} |a_j . rho|), gap = P(z) - Dual(theta)
+ * (clamped at 0).  The optimal dual point lies within sqrt(2 gap) / lambda of
+ * theta, so a coordinate j in S with |a_j . theta| + that radius x ||a_j|| < 1
+ * is zero in every solution.  Two margins keep the test safe when P, the
+ * dual value and the correlations carry FP32 rounding: the radius is
+ *   R = sqrt(2 (gap + eta (P + ||x||^2 / 2))) / lambda,  eta = 1e-6,
+ * and j is removed from S (mask = 0, z_j = 0) when
+ *   stat_j = |a_j . theta| + R ||a_j||  <  1 - tau,  tau = 1e-4.
+ * ||a_j|| is the norm of filter k restricted to the taps that land on the
+ * image.  stat: [H][W][K] (NAN off the incoming S; may be NULL); *gap_out
+ * (may be NULL).  Returns the number of coordinates left in S. */
+int64_t orc_screen_image(int K, int s, int H, int W, const double *d,
+                         const double *x, double *z, uint8_t *mask,
+                         double lambda, double *gap_out, double *stat);
+
+/* Proximal gradient on Eq. 3 as orc_code_update_image, with the screening test
+ * above run on the active set before iterations 0, e, 2e, ... (e =
+ * screen_every > 0; 0 = never).  mask is in/out (the active set left at the
+ * end); *gap_out is the gap of the last test.  Returns the active count. */
+int64_t orc_code_update_image_screened(int K, int s, int H, int W,
+                                       const double *d, const double *x,
+                                       double *z, uint8_t *mask, double alpha,
+                                       double lambda, int n_iters,
+                                       int screen_every, double *gap_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -486,3 +486,99 @@ def test_gauss_seidel_matches_explicit_matrices_and_descends():
         assert f1 <= f0 * (1 + 1e-12)  # a step of 1/L on one block never increases Eq. 5
         f0 = f1
     np.testing.assert_allclose(got, want, atol=1e-12)
+
+
+# ------------------------------------------------------------------ safe screening (Sec. 5)
+
+def _screen_problem(frac):
+    """10 x 10 image, K = 3 filters of 5 x 5, p = 1/2; lambda = frac x lambda_max
+    of the sampled set (lambda_max = max_S |a_j . x| from the explicit matrix)."""
+    K, s, H, W = 3, 5, 10, 10
+    d = I.filters(5, K, s).astype(np.float64)
+    x = I.images(6, [H], [W]).astype(np.float64)
+    A = explicit_synthesis_matrix(d.reshape(K, s, s), H, W)
+    m = R.mask_image(R.Config(K=K, s=s, p_num=1, p_den=2, seed=31), 1, 0, H, W).ravel()
+    S = np.flatnonzero(m)
+    lam_max = float(np.abs(A[:, S].T @ x).max())
+    cfg = R.Config(K=K, s=s, lam=frac * lam_max, p_num=1, p_den=2, seed=31)
+    return cfg, d, x, A, m, S, lam_max, H, W
+
+
+@pytest.mark.parametrize("frac", [0.2, 0.5, 0.8])
+def test_screening_never_removes_a_coordinate_of_the_solution(frac):
+    """Safety: every coordinate the test removes, at iterates near and far from
+    the optimum, is zero in the solution of Eq. 3 on the sampled set (30,000
+    PG iterations); close to the optimum it removes almost all zeros."""
+    cfg, d, x, A, m, S, _, H, W = _screen_problem(frac)
+    batch = R.Batch(H=[H], W=[W], ids=[0])
+    z_star = R.code_step(cfg, batch, x, d, np.zeros(m.size), t=1, n_iters=30000)
+    zeros = (m == 1) & (z_star == 0)
+    for its in [0, 5, 20, 100, 1000]:
+        z0 = R.code_step(cfg, batch, x, d, np.zeros(m.size), t=1, n_iters=its)
+        z, mm, gap, stat = R.screen_image(cfg, d, x, z0, m, H, W)
+        removed = (m == 1) & (mm == 0)
+        assert not np.any(removed & ~zeros), (its, np.abs(z_star[removed]).max())
+        assert gap >= 0.0 and not np.any(z[removed])
+        assert np.isnan(stat[m == 0]).all()
+    assert removed.sum() >= 0.9 * zeros.sum()
+    assert gap < 1e-4
+
+
+def test_screening_above_lambda_max_removes_every_coordinate():
+    """For lambda > lambda_max the solution is z = 0 and the gap at z = 0 is 0,
+    so the test removes the whole sampled set."""
+    cfg, d, x, A, m, S, lam_max, H, W = _screen_problem(1.05)
+    z, mm, gap, _ = R.screen_image(cfg, d, x, np.zeros(m.size), m, H, W)
+    assert gap == pytest.approx(0.0, abs=1e-12)
+    assert not mm.any() and not z.any()
+
+
+@pytest.mark.parametrize("frac", [0.7, 0.9])
+def test_screening_at_zero_contains_the_safe_rule(frac):
+    """At z = 0 the sphere test removes every coordinate the SAFE rule of
+    El Ghaoui et al. removes: |a_j . x| < lambda - ||a_j|| ||x|| (lambda_max -
+    lambda) / lambda_max (taken with 1% room for the test's margins)."""
+    cfg, d, x, A, m, S, lam_max, H, W = _screen_problem(frac)
+    lam = cfg.lam
+    corr = A.T @ x
+    norms = np.linalg.norm(A, axis=0)
+    safe = np.zeros(m.size, bool)
+    safe[S] = np.abs(corr[S]) < lam - norms[S] * np.linalg.norm(x) * (lam_max - lam) / lam_max \
+        - 0.01 * lam
+    assert safe.any()
+    _, mm, _, _ = R.screen_image(cfg, d, x, np.zeros(m.size), m, H, W)
+    assert not np.any(safe & (mm == 1))
+
+
+def test_screening_statistic_matches_explicit_matrix():
+    """Gap, dual point and the per-coordinate statistic from the explicit
+    matrix (columns by scipy convolve2d, column norms from those columns)."""
+    cfg, d, x, A, m, S, _, H, W = _screen_problem(0.5)
+    batch = R.Batch(H=[H], W=[W], ids=[0])
+    z0 = R.code_step(cfg, batch, x, d, np.zeros(m.size), t=1, n_iters=20)
+    _, _, gap, stat = R.screen_image(cfg, d, x, z0, m, H, W)
+    lam = cfg.lam
+    rho = x - A @ z0
+    scale = max(lam, float(np.abs(A[:, S].T @ rho).max()))
+    theta = rho / scale
+    primal = 0.5 * rho @ rho + lam * np.abs(z0).sum()
+    dual = 0.5 * x @ x - 0.5 * lam ** 2 * np.sum((theta - x / lam) ** 2)
+    assert gap == pytest.approx(primal - dual, rel=1e-10)
+    radius = np.sqrt(2 * (primal - dual + 1e-6 * (primal + 0.5 * x @ x))) / lam
+    want = np.abs(A[:, S].T @ theta) + radius * np.linalg.norm(A[:, S], axis=0)
+    np.testing.assert_allclose(stat[S], want, rtol=1e-10)
+
+
+def test_screened_code_step_reaches_the_unscreened_optimum():
+    """Screening every 50 iterations changes the iterates but not the limit:
+    both runs end at the solution of Eq. 3, and the active set keeps its
+    support while shrinking."""
+    cfg, d, x, A, m, S, _, H, W = _screen_problem(0.4)
+    batch = R.Batch(H=[H], W=[W], ids=[0])
+    z_plain = R.code_step(cfg, batch, x, d, np.zeros(m.size), t=1, n_iters=4000)
+    z_scr, active, gaps = R.code_step_screened(cfg, batch, x, d, np.zeros(m.size), t=1,
+                                               n_iters=4000, screen_every=50)
+    np.testing.assert_allclose(z_scr, z_plain, atol=1e-9)
+    assert np.all(active[z_plain != 0] == 1)
+    assert active.sum() < m.sum() and np.all(active <= m)
+    assert gaps[0] >= 0.0
