@@ -53,6 +53,12 @@ WORKLOADS = {
     "admm": dict(n=10, H=100, W=100, K=100, p=(1, 10), n_iters=10, solver="admm", cg_iters=20,
                  desc="ADMM code step: 10 x 100x100 blob images, K=100 11x11, p=1/10, lambda=1, "
                       "10 ADMM its x 20 CG steps/step (plain FP32 operators)"),
+    # safe screening (Sec. 5) on the 64 x 256^2 batch: the duality-gap sphere
+    # test before PG iterations 0, 25, 50 and 75 of each step
+    "screen": dict(n=64, H=256, W=256, K=100, p=(1, 4), n_iters=100, solver="screen",
+                   screen_every=25,
+                   desc="screened code step: 64 x 256x256 blob images, K=100 11x11, p=1/4, "
+                        "lambda=1, 100 PG its/step, gap-safe test every 25 its"),
 }
 
 
@@ -159,16 +165,32 @@ def measured_traffic(kernel: str, npx: int):
         return None
 
 
-def launches_per_step(path: str, n_iters: int) -> int:
-    """Kernels the library launches in one scsc_code_step (counted from the
-    host orchestration): mask 1; step size: stencils 2, power iteration
-    3 + 50 * 3 + 3; then
-    plain: apply-mask 1 + 2 per iteration;
-    tensor: filter images 1, segment counts 1, scan 3, pack 1, 3 per iteration, unpack 1."""
+def launches_per_step(wl, path: str, n_iters: int, n_images: int, per_image: bool) -> int:
+    """Kernels the library launches in one step of workload `wl` (counted from
+    the host orchestration).  Proximal gradient: mask 1; step size: stencils
+    2, power iteration 3 + 50 * 3 + 3; then per call on the active set
+    plain: apply-mask 1 + per iteration synthesis and adjoint (one launch per
+    image with per_image) and the observed-pixel mask when there is one;
+    tensor: filter images 1, segment counts 1, scan 3, pack 1, A tiles 1,
+    3 per iteration, unpack 1.  Screening adds 7 per test (apply-mask, tap
+    norms, synthesis, adjoint, statistics, per-image finish, test).  ADMM:
+    mask 1, init 1, A^T x 1, per iteration rhs 1, QP 3, CG init 1, dots 2,
+    per CG step QP 3 + dots 2 + update 2, shrink 1; final 1."""
+    obs = "observed" in wl
+
+    def pg(n):
+        if path == "fp32":
+            per_it = 2 * (n_images if per_image else 1) + (1 if obs else 0)
+            return 1 + per_it * n
+        return 1 + 1 + 3 + 1 + 1 + 3 * n + 1
+
+    if wl.get("solver") == "admm":
+        return 1 + 2 + n_iters * (1 + 3 + 1 + 2 + 7 * wl["cg_iters"] + 1) + 1
     base = 1 + 2 + (3 + 50 * 3 + 3)
-    if path == "fp32":
-        return base + 1 + 2 * n_iters
-    return base + 1 + 1 + 3 + 1 + 3 * n_iters + 1
+    if wl.get("solver") == "screen":
+        e = wl["screen_every"]
+        return base + sum(7 + pg(min(e, n_iters - i)) for i in range(0, n_iters, e))
+    return base + pg(n_iters)
 
 
 def cpu_baseline(wl, budget_s=20.0):
@@ -187,6 +209,8 @@ def cpu_baseline(wl, budget_s=20.0):
         if wl.get("solver") == "admm":
             m = R.mask_image(cfg, 1, int(ids[0]), int(H[0]), int(W[0])).ravel()
             R.admm_image(cfg, d, x, z, m, int(H[0]), int(W[0]), n, cg_iters=wl["cg_iters"])
+        elif wl.get("solver") == "screen":
+            R.code_step_screened(cfg, b, x, d, z, 1, n, wl["screen_every"], step=step)
         elif obs is None:
             R.code_step(cfg, b, x, d, z, 1, n, step=step)
         else:
@@ -201,7 +225,8 @@ def cpu_baseline(wl, budget_s=20.0):
     pf = int(H[0]) * int(W[0]) * wl["K"] * iters
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     what = (f"{iters} ADMM iterations x {wl['cg_iters']} CG steps" if wl.get("solver") == "admm"
-            else f"{iters} PG iterations")
+            else f"{iters} PG iterations, a screening test every {wl['screen_every']}"
+            if wl.get("solver") == "screen" else f"{iters} PG iterations")
     return {"value": pf / el / 1e9, "unit": "Gpix*filter/s", "cores": cores, "kind": "oracle",
             "sample": f"1 image {int(H[0])}x{int(W[0])} of the workload, K={wl['K']}, "
                       f"{what} (FP64, dense adjoint, OpenMP), {el:.1f} s"}
@@ -225,6 +250,8 @@ def run_reference(args, wl):
             m = R.mask_image(cfg, 1, int(ids[0]), int(H[0]), int(W[0])).ravel()
             return R.admm_image(cfg, d, x, z, m, int(H[0]), int(W[0]), n,
                                 cg_iters=wl["cg_iters"])
+        if wl.get("solver") == "screen":
+            return R.code_step_screened(cfg, b, x, d, z, 1, n, wl["screen_every"], step=step)[0]
         if obs is None:
             return R.code_step(cfg, b, x, d, z, 1, n, step=step)
         return R.code_step_observed(cfg, b, x, d, z, obs, 1, n, step=step)
@@ -399,12 +426,16 @@ def main():
     ctx = scsc.Context(K, 11, lam, wl["p"], seed=0, prec=args.prec, stream=stream, flags=flags)
     obs_np = make_observed(wl, rank, H, W)
     obs = torch.from_numpy(obs_np).cuda() if obs_np is not None else None
+    screen_stats = {}  # screened workload: the last call's t, mean gap and survivors
 
     def code_step(c, x_, d_, z_, t, o=None):
         """One code step of the workload (inpainting: observed pixels only;
         the ADMM workload: the ADMM solver)."""
         if wl.get("solver") == "admm":
             c.code_step_admm(batch, x_, d_, z_, t, n_iters, wl["cg_iters"])
+        elif wl.get("solver") == "screen":
+            gaps, kept = c.code_step_screened(batch, x_, d_, z_, t, n_iters, wl["screen_every"])
+            screen_stats.update(t=t, gap_mean=float(np.mean(gaps)), active=int(kept.sum()))
         elif obs is None:
             c.code_step(batch, x_, d_, z_, t, n_iters)
         else:
@@ -452,7 +483,7 @@ def main():
             code_step(ctx, x, d, z, 100 + i)
         ctx.sync()
         for name in ["synth_tc", "adj_tc", "finalize_r", "synth_fp32", "adjoint_fp32", "pack",
-                     "unpack", "power", "mask"]:
+                     "unpack", "power", "mask", "screen"]:
             tot, n = scsc.scsc_diag_kernel_time(ctx, name)
             if n:
                 kt[name] = (tot, n)
@@ -558,7 +589,15 @@ def main():
                "rel_obj_err_vs_fp32": rel_err,
                "e2e": {"value": e2e_val, "unit": "Gpix*filter/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h},
-               "gpu_launches": launches_per_step(args.prec, n_iters) * args.steps}
+               "gpu_launches": launches_per_step(wl, args.prec, n_iters, len(H),
+                                                 args.per_image) * args.steps}
+        if screen_stats:
+            with torch.cuda.stream(stream):
+                bits = ctx.mask(batch, screen_stats["t"]).cpu().numpy()
+            sampled = int(np.unpackbits(bits.view(np.uint8)).sum())
+            out["screening"] = {"sampled_coordinates": sampled,
+                                "active_after_last_test": screen_stats["active"],
+                                "mean_gap_at_last_test": screen_stats["gap_mean"]}
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(wl)
         print(json.dumps(out), flush=True)

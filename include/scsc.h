@@ -162,6 +162,38 @@ scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const fl
                                 const float *d_dev, float *z_dev, uint64_t t, int n_iters,
                                 int cg_iters, double rho, double alpha);
 
+/* Safe screening of the code problem (Sec. 5: the code subproblem is a sparse
+ * LASSO, and safe screening proves coordinates zero so that their updates can
+ * be skipped).  For each image, on its active set S = the set bits of bits_dev
+ * ([total_pixels][ceil(K/32)] words, the layout scsc_mask writes; in/out):
+ * codes off S are set to zero, then the duality-gap sphere test removes from S
+ * every coordinate it proves zero in every solution of Eq. 3 restricted to S,
+ * clearing its bit and its code.  With r = D z - x and g = D^T r:
+ *   scale = max(lambda, max_S |g|),
+ *   gap   = P(z) - Dual(-r / scale) >= 0  (P = 0.5 ||r||^2 + lambda ||z||_1,
+ *           Dual(theta) = 0.5 ||x||^2 - 0.5 lambda^2 ||theta - x / lambda||^2),
+ *   R     = sqrt(2 (gap + 1e-6 (P + 0.5 ||x||^2))) / lambda,
+ *   j leaves S when |g_j| / scale + R ||a_j|| < 1 - 1e-4,
+ * ||a_j|| the norm of filter k over the taps that land on the image; the two
+ * margins cover FP32 rounding.  Plain FP32 operators and FP64 reductions in
+ * either precision.  gap_host (n_images doubles, may be NULL): each image's
+ * duality gap at the input codes; n_active_host (n_images int64, may be NULL):
+ * the coordinates left in each image's set.  Synchronises the stream when an
+ * output is requested.  Errors as scsc_code_step. */
+scsc_status scsc_screen(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                        const float *d_dev, float *z_dev, uint32_t *bits_dev, double *gap_host,
+                        int64_t *n_active_host);
+
+/* scsc_code_step (step t, M^t, n_iters proximal-gradient iterations, Eq. 4
+ * codes out) with the test of scsc_screen run on the active set, initially
+ * M^t, before iterations 0, e, 2e, ... (e = screen_every >= 1); the iterations
+ * update the active coordinates only, and the removed ones stay zero.  The
+ * outputs are those of the last test (SCSC_EINVAL if one is requested with
+ * n_iters = 0).  SCSC_EINVAL for n_iters < 0 or screen_every < 1. */
+scsc_status scsc_code_step_screened(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                                    const float *d_dev, float *z_dev, uint64_t t, int n_iters,
+                                    int screen_every, double *gap_host, int64_t *n_active_host);
+
 /* Dictionary update.  SCSC_DICT_BATCH (Eq. 5): r = D z - x,
  * G_k(u,v) = sum_n sum_{i,j} r(i,j) z_k(i+c-u, j+c-v),
  * d_k <- P(d_k - G_k / L_d) with L_d from the power-iteration rule on

@@ -18,13 +18,14 @@ enum KernelId {
   KID_FINALIZE,
   KID_ADJ_TC,
   KID_UNPACK,
+  KID_SCREEN,
   KID_COUNT
 };
 
 inline const char *kernel_name(int id) {
   static const char *names[KID_COUNT] = {"mask",     "power",    "synth_fp32", "adjoint_fp32",
                                          "pack",     "synth_tc", "finalize_r", "adj_tc",
-                                         "unpack"};
+                                         "unpack",   "screen"};
   return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 

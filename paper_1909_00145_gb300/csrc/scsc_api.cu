@@ -76,6 +76,9 @@ struct scsc_ctx {
   DevBuf ddtG, ddtA;  // tap Gram matrix and per-class stencils of D D^T
   DevBuf admm;        // ADMM vectors: y, u, b, A^T x, CG residual, direction, QP image
   DevBuf admm_partials;  // per-image FP64 partials of the CG dot products
+  // screening: D^T r on the active set, per-filter tap prefix sums and norms,
+  // per-image partials, per-image results and survivor counts
+  DevBuf sg, spref, snrm, spart, simg, skept;
   // host-buffer entry: device copies of d and of two chunks of x and z, the
   // copy streams and the events that order them
   DevBuf hd, hx[2], hz[2];
@@ -420,9 +423,10 @@ scsc_status scsc_lipschitz_codes(scsc_ctx *ctx, const scsc_batch *batch, const f
 // scsc_code_step / scsc_code_step_observed (obs = NULL: every pixel observed).
 // keep_step: use the step parameters already in ctx->prm (the host-buffer
 // entry computes them once for the whole batch before its chunks).
+// keep_mask: iterate on the active set already in ctx->bits (screened steps).
 static scsc_status code_step_impl(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
                            const float *d_dev, float *z_dev, const uint8_t *obs, uint64_t t,
-                           int n_iters, bool keep_step = false) {
+                           int n_iters, bool keep_step = false, bool keep_mask = false) {
   if (!ctx) return SCSC_EINVAL;
   if (!x_dev || !d_dev || !z_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
   if (n_iters < 0) return fail(ctx, SCSC_EINVAL, "n_iters = %d < 0", n_iters);
@@ -430,7 +434,7 @@ static scsc_status code_step_impl(scsc_ctx *ctx, const scsc_batch *batch, const 
   const BatchDev &b = ctx->batch.view;
   const int K = ctx->cfg.K, s = ctx->cfg.s;
   cudaStream_t st = ctx->stream;
-  CKS(build_mask(ctx, t));
+  if (!keep_mask) CKS(build_mask(ctx, t));
   if (!keep_step) CKS(code_step_size(ctx, d_dev));
   const StepParams *prm = ctx->prm.as<StepParams>();
   if (ctx->cfg.prec == SCSC_BF16) {
@@ -659,6 +663,97 @@ scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const fl
   }
   CK(launch_admm_final(b, K, z_dev, y, bits, st));
   return SCSC_OK;
+}
+
+// The screening test on the staged batch's active set `bits` (enqueued only):
+// z <- z on the set (skipped when the caller knows z is zero off the set);
+// r = D z - x; g = D^T r on the set; per-image gap and radius; bits and codes
+// of the removed coordinates cleared; survivors counted into skept.
+static scsc_status screen_enqueue(scsc_ctx *ctx, const float *x_dev, const float *d_dev,
+                                  float *z_dev, uint32_t *bits, bool zero_off_set = true) {
+  const BatchDev &b = ctx->batch.view;
+  const int K = ctx->cfg.K, s = ctx->cfg.s;
+  cudaStream_t st = ctx->stream;
+  CK(ctx->r.ensure((size_t)b.total_px * 4));
+  CK(ctx->sg.ensure((size_t)b.total_px * K * 4));
+  CK(ctx->spref.ensure((size_t)K * (s + 1) * (s + 1) * 8));
+  CK(ctx->snrm.ensure((size_t)K * 4));
+  CK(ctx->spart.ensure((size_t)b.n * kScreenBlocks * 5 * 8));
+  CK(ctx->simg.ensure((size_t)b.n * sizeof(ScreenImage)));
+  CK(ctx->skept.ensure((size_t)b.n * 8));
+  float *r = ctx->r.as<float>(), *g = ctx->sg.as<float>();
+  if (zero_off_set) CK(launch_apply_mask_dense(b, K, bits, z_dev, st));
+  CK(launch_screen_prepare(d_dev, K, s, ctx->spref.as<double>(), ctx->snrm.as<float>(), st));
+  int p1 = ctx->prof.begin(KID_SYNTH_FP32, st);
+  CK(launch_synth_fp32(b, K, s, d_dev, z_dev, nullptr, x_dev, r, st));
+  ctx->prof.end(p1, st);
+  int p2 = ctx->prof.begin(KID_ADJ_FP32, st);
+  CK(launch_adjoint_fp32(b, K, s, d_dev, r, bits, 0, nullptr, g, st));
+  ctx->prof.end(p2, st);
+  int p3 = ctx->prof.begin(KID_SCREEN, st);
+  CK(launch_screen_stats(b, K, x_dev, r, z_dev, g, bits, ctx->spart.as<double>(), st));
+  CK(launch_screen_finish(b.n, ctx->spart.as<double>(), ctx->cfg.lambda,
+                          ctx->simg.as<ScreenImage>(), st));
+  CK(cudaMemsetAsync(ctx->skept.p, 0, (size_t)b.n * 8, st));
+  CK(launch_screen_test(b, K, s, g, bits, z_dev, ctx->simg.as<ScreenImage>(),
+                        ctx->spref.as<double>(), ctx->snrm.as<float>(),
+                        ctx->skept.as<unsigned long long>(), st));
+  ctx->prof.end(p3, st);
+  return SCSC_OK;
+}
+
+// Per-image gaps and survivor counts of the last test, to the host.
+static scsc_status screen_outputs(scsc_ctx *ctx, double *gap_host, int64_t *n_active_host) {
+  const int n = ctx->batch.view.n;
+  cudaStream_t st = ctx->stream;
+  if (!gap_host && !n_active_host) return SCSC_OK;
+  std::vector<ScreenImage> img(n);
+  CK(cudaMemcpyAsync(img.data(), ctx->simg.p, (size_t)n * sizeof(ScreenImage),
+                     cudaMemcpyDeviceToHost, st));
+  if (n_active_host)
+    CK(cudaMemcpyAsync(n_active_host, ctx->skept.p, (size_t)n * 8, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (gap_host)
+    for (int i = 0; i < n; ++i) gap_host[i] = img[i].gap;
+  return SCSC_OK;
+}
+
+scsc_status scsc_screen(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                        const float *d_dev, float *z_dev, uint32_t *bits_dev, double *gap_host,
+                        int64_t *n_active_host) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!x_dev || !d_dev || !z_dev || !bits_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
+  CKS(stage_batch(ctx, batch));
+  CKS(screen_enqueue(ctx, x_dev, d_dev, z_dev, bits_dev));
+  return screen_outputs(ctx, gap_host, n_active_host);
+}
+
+scsc_status scsc_code_step_screened(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
+                                    const float *d_dev, float *z_dev, uint64_t t, int n_iters,
+                                    int screen_every, double *gap_host, int64_t *n_active_host) {
+  if (!ctx) return SCSC_EINVAL;
+  if (!x_dev || !d_dev || !z_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
+  if (n_iters < 0) return fail(ctx, SCSC_EINVAL, "n_iters = %d < 0", n_iters);
+  if (screen_every < 1) return fail(ctx, SCSC_EINVAL, "screen_every = %d < 1", screen_every);
+  CKS(stage_batch(ctx, batch));
+  CKS(build_mask(ctx, t));
+  CKS(code_step_size(ctx, d_dev));
+  uint32_t *bits = ctx->bits.as<uint32_t>();
+  if (n_iters == 0) CK(launch_apply_mask_dense(ctx->batch.view, ctx->cfg.K, bits, z_dev,
+                                               ctx->stream));
+  for (int it = 0; it < n_iters; it += screen_every) {
+    // after the first proximal-gradient chunk the codes are zero off the set
+    CKS(screen_enqueue(ctx, x_dev, d_dev, z_dev, bits, /*zero_off_set=*/it == 0));
+    const int chunk = std::min(screen_every, n_iters - it);
+    CKS(code_step_impl(ctx, batch, x_dev, d_dev, z_dev, nullptr, t, chunk, /*keep_step=*/true,
+                       /*keep_mask=*/true));
+  }
+  if (n_iters == 0) {
+    if (gap_host || n_active_host)
+      return fail(ctx, SCSC_EINVAL, "n_iters = 0: no screening test ran");
+    return SCSC_OK;
+  }
+  return screen_outputs(ctx, gap_host, n_active_host);
 }
 
 scsc_status scsc_objective_observed(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,

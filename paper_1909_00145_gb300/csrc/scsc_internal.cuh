@@ -143,5 +143,29 @@ cudaError_t launch_power_finish(const double *partials, int n_blocks, double saf
 cudaError_t launch_project_step(float *d, const float *G_or_null, const double *Gd_or_null,
                                 const double *L, int K, int M, cudaStream_t st);
 cudaError_t launch_check_finite(const float *a, int64_t n, int *flag, cudaStream_t st);
+// Safe screening of the code problem (kernels_screen.cu): duality-gap sphere
+// test per image on its active set.  prepare: per-filter prefix sums of the
+// squared taps (pref, K (s+1)^2 doubles) and norms (nrm, K floats); stats:
+// kScreenBlocks * 5 FP64 partials per image from r = D z - x, x, and z, g
+// on the set; finish: one ScreenImage per image; test:
+// clears the bits (and codes) of the coordinates the test removes and adds
+// the survivors of image n to kept[n].
+constexpr int kScreenBlocks = 64;
+struct ScreenImage {
+  double gap;        // duality gap at the tested codes (>= 0)
+  double primal;     // the code problem's objective at the tested codes
+  double inv_scale;  // 1 / max(lambda, max |g| on the set)
+  double radius;     // sphere radius with the rounding margin
+};
+cudaError_t launch_screen_prepare(const float *d, int K, int s, double *pref, float *nrm,
+                                  cudaStream_t st);
+cudaError_t launch_screen_stats(const BatchDev &b, int K, const float *x, const float *r,
+                                const float *z, const float *g, const uint32_t *bits,
+                                double *part, cudaStream_t st);
+cudaError_t launch_screen_finish(int n_img, const double *part, double lambda, ScreenImage *img,
+                                 cudaStream_t st);
+cudaError_t launch_screen_test(const BatchDev &b, int K, int s, const float *g, uint32_t *bits,
+                               float *z, const ScreenImage *img, const double *pref,
+                               const float *nrm, unsigned long long *kept, cudaStream_t st);
 
 }  // namespace scsc

@@ -63,6 +63,10 @@ _SIGNATURES = {
                             c_u64, c_int],
     "scsc_code_step_admm": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p,
                             c_u64, c_int, c_int, c_double, c_double],
+    "scsc_screen": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p, c_void_p,
+                    c_void_p, c_void_p],
+    "scsc_code_step_screened": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p,
+                                c_void_p, c_u64, c_int, c_int, c_void_p, c_void_p],
     "scsc_dict_step": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p, c_void_p, c_int,
                        c_u64],
     "scsc_objective_observed": [c_void_p, ctypes.POINTER(scsc_batch), c_void_p, c_void_p,
@@ -202,6 +206,12 @@ class Context:
     def code_step_admm(self, batch, x, d, z, t, n_iters, cg_iters, rho=0.0, alpha=0.0):
         return scsc_code_step_admm(self, batch, x, d, z, t, n_iters, cg_iters, rho, alpha)
 
+    def screen(self, batch, x, d, z, bits):
+        return scsc_screen(self, batch, x, d, z, bits)
+
+    def code_step_screened(self, batch, x, d, z, t, n_iters, screen_every):
+        return scsc_code_step_screened(self, batch, x, d, z, t, n_iters, screen_every)
+
     def objective_observed(self, batch, x, z, d, observed) -> float:
         return scsc_objective_observed(self, batch, x, z, d, observed)
 
@@ -297,6 +307,34 @@ def scsc_code_step_admm(ctx: Context, batch: Batch, x, d, z, t: int, n_iters: in
     _check(lib().scsc_code_step_admm(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d), _ptr(z),
                                      t, n_iters, cg_iters, float(rho), float(alpha)), ctx.handle,
            "scsc_code_step_admm")
+
+
+def scsc_screen(ctx: Context, batch: Batch, x, d, z, bits):
+    """Safe screening test on the active set `bits` (int32 device tensor in
+    the scsc_mask layout; updated in place, as are the codes z).  Returns
+    (per-image duality gaps, per-image active counts) as numpy arrays."""
+    import numpy as np
+    gaps = np.zeros(batch.n, dtype=np.float64)
+    kept = np.zeros(batch.n, dtype=np.int64)
+    _check(lib().scsc_screen(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d), _ptr(z),
+                             _ptr(bits), gaps.ctypes.data, kept.ctypes.data), ctx.handle,
+           "scsc_screen")
+    return gaps, kept
+
+
+def scsc_code_step_screened(ctx: Context, batch: Batch, x, d, z, t: int, n_iters: int,
+                            screen_every: int):
+    """Code step with the screening test every `screen_every` iterations.
+    Returns (per-image gaps, per-image active counts) of the last test."""
+    import numpy as np
+    gaps = np.zeros(batch.n, dtype=np.float64)
+    kept = np.zeros(batch.n, dtype=np.int64)
+    _check(lib().scsc_code_step_screened(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d),
+                                         _ptr(z), t, n_iters, screen_every,
+                                         gaps.ctypes.data if n_iters > 0 else None,
+                                         kept.ctypes.data if n_iters > 0 else None), ctx.handle,
+           "scsc_code_step_screened")
+    return gaps, kept
 
 
 def scsc_objective_observed(ctx: Context, batch: Batch, x, z, d, observed) -> float:
