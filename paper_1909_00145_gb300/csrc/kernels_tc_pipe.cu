@@ -74,9 +74,10 @@ __device__ __forceinline__ void load_masks(const Item &it, int a, int KW, const 
   po = pxoff[(int64_t)(it.q_row0 + a) * kStrip + e];
 }
 
-// 16-bit sampled mask of filter chunk c from a pixel's mask words.
-__device__ __forceinline__ uint32_t chunk_bits(const uint32_t (&mw)[4], int c) {
-  return (mw[c >> 1] >> ((c & 1) * 16)) & 0xFFFFu;
+// Mask word w of a pixel's four (0 past the end), by selects, so that a
+// runtime index keeps the words in registers.
+__device__ __forceinline__ uint32_t pick4(const uint32_t (&mw)[4], int w) {
+  return w == 0 ? mw[0] : w == 1 ? mw[1] : w == 2 ? mw[2] : w == 3 ? mw[3] : 0u;
 }
 
 // One bulk copy of an item's packed codes [beg, end) (16-byte aligned, a
@@ -327,12 +328,13 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
     tc::cp_async_wait<0>();
   } else {
     // ------------------------------------------------ epilogue: prox on packed codes
-    // thread e: pixel px = e & 127 (TMEM lane), group gi = chunks [c_lo, c_hi)
+    // thread e: pixel px = e & 127 (TMEM lane), group gi = units of 8 filters
+    // [u_lo, u_hi): the groups split the 2 NC units evenly, at most 8 each
     constexpr int kE = 128 * L::kEpi;  // epilogue threads (named barrier 1)
     const int e = tid - 128, px = e & 127, gi = e >> 7, ew = px >> 5;
-    const int npair = (NC + 1) / 2;  // chunk pairs share a TMEM load; groups split the pairs
-    const int c_lo = 2 * (gi * npair / L::kEpi);
-    const int c_hi = min(NC, 2 * ((gi + 1) * npair / L::kEpi));
+    const int u_lo = gi * 2 * NC / L::kEpi, u_hi = (gi + 1) * 2 * NC / L::kEpi;
+    const int nu = u_hi - u_lo;
+    const int w0 = (8 * u_lo) >> 5, sh = (8 * u_lo) & 31;  // mask word and bit of unit u_lo
     const float alpha = prm->alpha, thr = prm->thresh;
     const int n_items = q_end - q_begin;
     const uint32_t lane_base = taddr + ((uint32_t)(32 * ew) << 16);
@@ -362,11 +364,17 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
         staged = i + 2;
         load_masks(nxt, nxt.a, KW, bits, pxoff, px, mwn, pon);
       }
-      // this pixel's first value of chunk c_lo inside the staged item
+      // this group's mask bits (8 per unit, from bit 8 u_lo) and the pixel's
+      // first value of unit u_lo inside the staged item
+      const uint32_t m0 = pick4(mw, w0), m1 = pick4(mw, w0 + 1), m2 = pick4(mw, w0 + 2);
+      const uint64_t m01 = ((uint64_t)m1 << 32) | m0;
+      const uint64_t gmask = sh ? (m01 >> sh) | ((uint64_t)m2 << (64 - sh)) : m01;
       uint32_t first = po;
 #pragma unroll
-      for (int c = 0; c < kMaxNC; ++c)
-        if (c < c_lo) first += __popc(chunk_bits(mw, c));
+      for (int w = 0; w < 4; ++w) {
+        const int nb = min(32, max(0, 8 * u_lo - 32 * w));  // bits of word w below unit u_lo
+        first += __popc(nb == 32 ? mw[w] : (mw[w] & ((1u << nb) - 1u)));
+      }
       const int b = i & 1;
       bool okw = tc::mbar_wait_abortable(&stg_full[i & 1], (uint32_t)((i >> 1) & 1), abort_v,
                                          kWaitNs);
@@ -377,52 +385,55 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
       float *dv = vals(i & 1);
       // this item's A tile for the next synthesis (dense BF16 codes)
       uint8_t *const atile = abuf + (size_t)q * kStrip * Kp * 2;
-      uint32_t g[32];  // accumulator columns of two chunks (32 filters)
+      uint32_t g[32];  // accumulator columns of up to 4 units (32 filters)
       // running address of the pixel's next sampled value (filter order)
       uint32_t a_run = tc::smem_u32(dv) + 4u * first;
+      // two batches of at most 4 units: all loads of a batch, one wait
 #pragma unroll
-      for (int c = 0; c < kMaxNC; ++c) {
-        if (c < c_lo) continue;
-        if (c >= c_hi) break;
-        const uint32_t mc = chunk_bits(mw, c);
-        if (((c - c_lo) & 1) == 0) {  // c_lo is even: pairs (c, c + 1) share one load
-          __syncwarp();
-          tc::tmem_ld32_nowait(lane_base + b * 128 + 16 * c, g);
-          tc::tmem_ld_wait();
+      for (int bt = 0; bt < 2; ++bt) {
+        if (4 * bt >= nu) break;
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (4 * bt + j < nu)
+            tc::tmem_ld8_nowait(lane_base + b * 128 + 8 * (u_lo + 4 * bt + j),
+                                *reinterpret_cast<uint32_t(*)[8]>(&g[8 * j]));
+        tc::tmem_ld_wait();
+        tc::reg_fence(g);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int jj = 4 * bt + j;
+          if (jj >= nu) break;
+          const uint32_t mu = (uint32_t)(gmask >> (8 * jj)) & 0xFFu;
+          // slot of filter e2 = the running address: all loads are
+          // independent, then all stores.  Loads are unconditional (an
+          // unsampled filter's address still lies inside the staged item) and
+          // stores predicated, so the loop has no branches.
+          float zv[8], res[8];
+          uint32_t ad[8];
+#pragma unroll
+          for (int e2 = 0; e2 < 8; ++e2) {
+            ad[e2] = a_run;
+            a_run += ((mu >> e2) & 1u) << 2;
+          }
+#pragma unroll
+          for (int e2 = 0; e2 < 8; ++e2) zv[e2] = tc::ld_shared(ad[e2]);
+#pragma unroll
+          for (int e2 = 0; e2 < 8; ++e2) {
+            const float gv = __uint_as_float(g[8 * j + e2]);
+            const float v = zv[e2] - alpha * gv;  // soft threshold as v - clamp(v, -thr, thr)
+            res[e2] = v - fminf(fmaxf(v, -thr), thr);
+            tc::st_shared_if(ad[e2], res[e2], (mu >> e2) & 1u);
+          }
+          // the pixel's 8 filters of the A tile: the new codes in BF16, zero
+          // off the sample (K-major core of 8 pixels x 8 filters)
+#pragma unroll
+          for (int e2 = 0; e2 < 8; ++e2) res[e2] = ((mu >> e2) & 1u) ? res[e2] : 0.0f;
+          *reinterpret_cast<uint4 *>(atile + (size_t)(u_lo + jj) * 2048 + (px >> 3) * 128 +
+                                     (px & 7) * 16) =
+              make_uint4(pack_bf16x2(res[0], res[1]), pack_bf16x2(res[2], res[3]),
+                         pack_bf16x2(res[4], res[5]), pack_bf16x2(res[6], res[7]));
         }
-        // slot of filter e2 = the running address: all loads are independent,
-        // then all stores.  Loads are unconditional (an unsampled filter's
-        // address still lies inside the staged item) and stores predicated,
-        // so the loop has no branches.
-        float zv[16];
-        uint32_t ad[16];
-#pragma unroll
-        for (int e2 = 0; e2 < 16; ++e2) {
-          ad[e2] = a_run;
-          a_run += ((mc >> e2) & 1u) << 2;
-        }
-#pragma unroll
-        for (int e2 = 0; e2 < 16; ++e2)
-          zv[e2] = tc::ld_shared(ad[e2]);
-        float res[16];
-#pragma unroll
-        for (int e2 = 0; e2 < 16; ++e2) {
-          const float gv = __uint_as_float(g[(c & 1) * 16 + e2]);
-          const float v = zv[e2] - alpha * gv;  // soft threshold as v - clamp(v, -thr, thr)
-          res[e2] = v - fminf(fmaxf(v, -thr), thr);
-          tc::st_shared_if(ad[e2], res[e2], (mc >> e2) & 1u);
-        }
-        // the pixel's row of the A tile: the new codes in BF16, zero off the
-        // sample (K-major cores of 8 pixels x 8 filters, as the MMA reads them)
-#pragma unroll
-        for (int e2 = 0; e2 < 16; ++e2) res[e2] = ((mc >> e2) & 1u) ? res[e2] : 0.0f;
-        uint8_t *const arow = atile + (size_t)(2 * c) * 2048 + (px >> 3) * 128 + (px & 7) * 16;
-        *reinterpret_cast<uint4 *>(arow) =
-            make_uint4(pack_bf16x2(res[0], res[1]), pack_bf16x2(res[2], res[3]),
-                       pack_bf16x2(res[4], res[5]), pack_bf16x2(res[6], res[7]));
-        *reinterpret_cast<uint4 *>(arow + 2048) =
-            make_uint4(pack_bf16x2(res[8], res[9]), pack_bf16x2(res[10], res[11]),
-                       pack_bf16x2(res[12], res[13]), pack_bf16x2(res[14], res[15]));
       }
       tc::fence_before_sync();
       tc::fence_proxy_async();  // the updated codes, to the bulk copy below
