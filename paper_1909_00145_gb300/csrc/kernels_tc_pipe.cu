@@ -388,18 +388,22 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
       uint32_t g[32];  // accumulator columns of up to 4 units (32 filters)
       // running address of the pixel's next sampled value (filter order)
       uint32_t a_run = tc::smem_u32(dv) + 4u * first;
-      // two batches of at most 4 units: all loads of a batch, one wait
+      // two batches of at most 4 units, one wait each; a unit of the second
+      // batch is loaded into the registers of the first batch's unit j as
+      // soon as that unit is done, so its load overlaps the rest of the batch
+      auto load_unit = [&](int jj) {
+        tc::tmem_ld8_nowait(lane_base + b * 128 + 8 * (u_lo + jj),
+                            *reinterpret_cast<uint32_t(*)[8]>(&g[8 * (jj & 3)]));
+      };
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j < nu) load_unit(j);
+      tc::tmem_ld_wait();
+      tc::reg_fence(g);
 #pragma unroll
       for (int bt = 0; bt < 2; ++bt) {
         if (4 * bt >= nu) break;
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (4 * bt + j < nu)
-            tc::tmem_ld8_nowait(lane_base + b * 128 + 8 * (u_lo + 4 * bt + j),
-                                *reinterpret_cast<uint32_t(*)[8]>(&g[8 * j]));
-        tc::tmem_ld_wait();
-        tc::reg_fence(g);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int jj = 4 * bt + j;
@@ -433,6 +437,14 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
                                      (px & 7) * 16) =
               make_uint4(pack_bf16x2(res[0], res[1]), pack_bf16x2(res[2], res[3]),
                          pack_bf16x2(res[4], res[5]), pack_bf16x2(res[6], res[7]));
+          if (bt == 0 && jj + 4 < nu) {
+            __syncwarp();
+            load_unit(jj + 4);
+          }
+        }
+        if (bt == 0 && nu > 4) {
+          tc::tmem_ld_wait();
+          tc::reg_fence(g);
         }
       }
       tc::fence_before_sync();
