@@ -31,7 +31,6 @@ namespace {
 using namespace tcitems;
 
 constexpr uint64_t kWaitNs = 1000000000ull;
-constexpr int kMaxNC = 8;  // Kp <= 128
 
 // Offset the dynamic shared-memory base to a 1024-byte boundary by pointer
 // arithmetic on the shared array itself, so that the compiler keeps treating
@@ -82,7 +81,7 @@ __device__ __forceinline__ uint32_t pick4(const uint32_t (&mw)[4], int w) {
 
 // One bulk copy of an item's packed codes [beg, end) (16-byte aligned, a
 // multiple of 4 floats) into shared memory; `bar` completes when it lands.
-// Issued by one thread, after a barrier that retired all earlier reads of dv.
+// Issued by one thread once every reader of dv's previous contents is done.
 __device__ __forceinline__ void stage_item(uint64_t beg, uint64_t end, const float *packed,
                                            float *dv, uint64_t *bar) {
   const uint32_t bytes = (uint32_t)(end - beg) * 4u;
@@ -114,7 +113,8 @@ struct Adj2 {
   // Epilogue: kEpi groups of four warps; each covers all 128 pixels (TMEM lane
   // quarters) and a share of the filter chunks.
   static constexpr int kEpi = 2;
-  static constexpr int kThreads = 32 * (1 + kProd + 4 * kEpi);
+  // warp 0: MMA; 1..kProd: residual rows; then 4 kEpi epilogue warps; last: copies
+  static constexpr int kThreads = 32 * (1 + kProd + 4 * kEpi + 1);
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)S * Kp * 32; }
   __host__ __device__ static size_t vals_bytes(int Kp) { return (size_t)kStrip * Kp * 4; }
   __host__ __device__ static size_t mask_bytes(int KW) { return (size_t)kStrip * KW * 4; }
@@ -326,44 +326,30 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
       sbuf ^= 1;
     }
     tc::cp_async_wait<0>();
-  } else {
+  } else if (warp <= L::kProd + 4 * L::kEpi) {
     // ------------------------------------------------ epilogue: prox on packed codes
     // thread e: pixel px = e & 127 (TMEM lane), group gi = units of 8 filters
-    // [u_lo, u_hi): the groups split the 2 NC units evenly, at most 8 each
-    constexpr int kE = 128 * L::kEpi;  // epilogue threads (named barrier 1)
-    const int e = tid - 128, px = e & 127, gi = e >> 7, ew = px >> 5;
+    // [u_lo, u_hi): the groups split the 2 NC units evenly, at most 8 each.
+    // The warps run unsynchronised with one another: lane 0 of each waits on
+    // the item's staged codes and accumulator, and arrives on tempty when the
+    // warp is done with the item (TMEM, the staged codes and the A tile).
+    const int e = tid - 32 * (1 + L::kProd), px = e & 127, gi = e >> 7, ew = px >> 5;
     const int u_lo = gi * 2 * NC / L::kEpi, u_hi = (gi + 1) * 2 * NC / L::kEpi;
     const int nu = u_hi - u_lo;
     const int w0 = (8 * u_lo) >> 5, sh = (8 * u_lo) & 31;  // mask word and bit of unit u_lo
     const float alpha = prm->alpha, thr = prm->thresh;
     const int n_items = q_end - q_begin;
     const uint32_t lane_base = taddr + ((uint32_t)(32 * ew) << 16);
-    // item bookkeeping one step ahead: cur = item i, nxt = item i + 1;
-    // b0v..b2v = seg_base of items i, i + 1, i + 2 (b3v loaded a step early)
+    // item bookkeeping one step ahead: cur = item i, nxt = item i + 1
     Item cur = item_of(im, q_begin), nxt = cur;
-    uint64_t b0v = 0, b1v = 0, b2v = 0;
     uint32_t mw[4], mwn[4], po = 0, pon = 0;
     if (n_items > 0) {
-      b0v = seg_base[q_begin];
-      b1v = seg_base[q_begin + 1];
-      if (e == 0) stage_item(b0v, b1v, packed, vals(0), &stg_full[0]);
       load_masks(cur, cur.a, KW, bits, pxoff, px, mw, po);
       if (n_items > 1) nxt = next_item(im, cur);
-      b2v = seg_base[min(q_begin + 2, Q)];
     }
-    int staged = n_items > 0 ? 1 : 0;  // items whose staging copy was issued: [0, staged)
-    int i = 0;
-    for (; i < n_items; ++i) {
+    for (int i = 0; i < n_items; ++i) {
       const int q = q_begin + i;
-      const uint64_t b3v = seg_base[min(q + 3, Q)];
-      if (i + 1 < n_items) {
-        if (e == 0) {
-          tc::bulk_wait_read0();  // item i - 1's write-back has left the buffer
-          stage_item(b1v, b2v, packed, vals((i + 1) & 1), &stg_full[(i + 1) & 1]);
-        }
-        staged = i + 2;
-        load_masks(nxt, nxt.a, KW, bits, pxoff, px, mwn, pon);
-      }
+      if (i + 1 < n_items) load_masks(nxt, nxt.a, KW, bits, pxoff, px, mwn, pon);
       // this group's mask bits (8 per unit, from bit 8 u_lo) and the pixel's
       // first value of unit u_lo inside the staged item
       const uint32_t m0 = pick4(mw, w0), m1 = pick4(mw, w0 + 1), m2 = pick4(mw, w0 + 2);
@@ -376,13 +362,17 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
         first += __popc(nb == 32 ? mw[w] : (mw[w] & ((1u << nb) - 1u)));
       }
       const int b = i & 1;
-      bool okw = tc::mbar_wait_abortable(&stg_full[i & 1], (uint32_t)((i >> 1) & 1), abort_v,
-                                         kWaitNs);
-      if (e == 0 && okw)
-        okw = tc::mbar_wait_abortable(&tfull[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
-      if (tc::named_sync_or(1, kE, !okw)) break;
+      bool okw = true;
+      if (lane == 0) {
+        okw = tc::mbar_wait_abortable(&stg_full[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
+        if (okw)
+          okw = tc::mbar_wait_abortable(&tfull[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs);
+      }
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) break;
+      __syncwarp();
       tc::fence_after_sync();
-      float *dv = vals(i & 1);
+      float *dv = vals(b);
       // this item's A tile for the next synthesis (dense BF16 codes)
       uint8_t *const atile = abuf + (size_t)q * kStrip * Kp * 2;
       uint32_t g[32];  // accumulator columns of up to 4 units (32 filters)
@@ -448,31 +438,46 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
         }
       }
       tc::fence_before_sync();
-      tc::fence_proxy_async();  // the updated codes, to the bulk copy below
+      tc::fence_proxy_async();  // the updated codes, to the copy warp's bulk write-back
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&tempty[b]);
-      tc::named_sync(1, kE);
-      // write-back: one bulk copy; the thread that issues it waits for its
-      // reads before it refills this buffer (prefetch two items on)
-      if (e == 0 && b1v > b0v) {
-        tc::bulk_s2g(packed + b0v, dv, (uint32_t)(b1v - b0v) * 4u);
-        tc::bulk_commit();
-      }
 #pragma unroll
       for (int w = 0; w < 4; ++w) mw[w] = mwn[w];
       po = pon;
-      b0v = b1v;
-      b1v = b2v;
-      b2v = b3v;
       if (i + 2 < n_items) nxt = next_item(im, nxt);
     }
-    if (e == 0) {
-      // staging copies issued but not consumed (after an abort) land, and the
-      // write-backs complete, before the CTA exits
-      for (int j = i; j < staged; ++j)
-        tc::mbar_wait_bounded(&stg_full[j & 1], (uint32_t)((j >> 1) & 1), kWaitNs);
-      tc::bulk_wait0();
+  } else if (lane == 0) {
+    // ------------------------------------------------ copy warp: staging and write-back
+    // Item i's packed codes come into buffer i & 1 by one bulk copy
+    // (stg_full[i & 1]); once every epilogue warp has arrived on tempty for
+    // item i, they go back to HBM by one bulk copy, and when that copy has
+    // read the buffer, item i + 2 is staged into it.
+    const int n_items = q_end - q_begin;
+    int staged = 0;  // items whose staging copy was issued: [0, staged)
+    for (; staged < 2 && staged < n_items; ++staged)
+      stage_item(seg_base[q_begin + staged], seg_base[q_begin + staged + 1], packed,
+                 vals(staged), &stg_full[staged]);
+    int i = 0;
+    for (; i < n_items; ++i) {
+      const int b = i & 1;
+      if (!tc::mbar_wait_abortable(&tempty[b], (uint32_t)((i >> 1) & 1), abort_v, kWaitNs)) break;
+      const uint64_t beg = seg_base[q_begin + i], end = seg_base[q_begin + i + 1];
+      if (end > beg) {
+        tc::bulk_s2g(packed + beg, vals(b), (uint32_t)(end - beg) * 4u);
+        tc::bulk_commit();
+      }
+      if (i + 2 < n_items) {
+        tc::bulk_wait_read0();  // the write-back has read the buffer
+        stage_item(seg_base[q_begin + i + 2], seg_base[q_begin + i + 3], packed, vals(b),
+                   &stg_full[b]);
+        staged = i + 3;
+      }
     }
+    // staging copies issued but not consumed (after an abort) land, and the
+    // write-backs complete, before the CTA exits
+    for (int j = i; j < staged; ++j)
+      tc::mbar_wait_bounded(&stg_full[j & 1], (uint32_t)((j >> 1) & 1), kWaitNs);
+    tc::bulk_wait0();
   }
 
   __syncthreads();
