@@ -75,6 +75,18 @@ def make_inputs(wl, rank):
     return H, W, ids, x, d
 
 
+def reduce_over_ranks(v: float, op: str, device) -> float:
+    """max or sum of a per-rank scalar over the ranks of the process group
+    (the value itself with one rank or none)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def make_observed(wl, rank, H, W):
     """Observation mask of an inpainting workload (None for the others)."""
     from paper_1909_00145_gb300 import inputs as I
@@ -464,13 +476,11 @@ def main():
         clocks = sampler.stop()
         ctx.sync()
         barrier()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    # each rank runs its own batch (its own image ids; C5's sizes differ per
+    # rank): the job's units are summed, its time is the slowest rank's
+    ms = reduce_over_ranks(e0.elapsed_time(e1), "max", "cuda")
     per_step_ms = ms / args.steps
-    units = npx * K * n_iters * args.steps * world
+    units = reduce_over_ranks(float(npx * K * n_iters * args.steps), "sum", "cuda")
     value = units / (ms / 1e3) / 1e9
 
     # per-kernel device times: the same steps again with CUDA events around
@@ -563,11 +573,9 @@ def main():
             zh.copy_(zd, non_blocking=True)
             stream.synchronize()
         e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = npx * K * n_iters * args.e2e_steps * world / e2e_s / 1e9
+    e2e_s = reduce_over_ranks(e2e_s, "max", "cuda")
+    e2e_units = reduce_over_ranks(float(npx * K * n_iters * args.e2e_steps), "sum", "cuda")
+    e2e_val = e2e_units / e2e_s / 1e9
     h2d = x.numel() * 4 + d.numel() * 4 + z.numel() * 4 + (obs.numel() if obs is not None else 0)
     d2h = z.numel() * 4
 
