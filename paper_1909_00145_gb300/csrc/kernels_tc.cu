@@ -160,24 +160,45 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int K
   float *zb = z + (it.base + (int64_t)it.a * it.W + it.js * kStrip) * K;
   const int n = npx * K;
   // (pixel, filter) of element j, advanced by kThreads elements per step
-  // without a division
+  // without a division; kU elements per round, every load issued before any
+  // store (the loop is bound by memory latency otherwise)
+  constexpr int kU = 4;
   int pl = threadIdx.x / K, k = threadIdx.x - pl * K;
   const int dpl = kThreads / K, dk = kThreads - dpl * K;
-  for (int j = threadIdx.x; j < n; j += kThreads) {
-    const int c = k >> 4, e = k & 15;
-    const uint32_t m = s_m[c][pl];
-    if ((m >> e) & 1u) {
-      const uint64_t idx = item_base + s_off[c][pl] + __popc(m & ((1u << e) - 1u));
-      if (mode == 0) packed[idx] = zb[j];
-      else zb[j] = packed[idx];
-    } else if (mode == 1) {
-      zb[j] = 0.0f;
+  for (int j0 = threadIdx.x; j0 < n; j0 += kU * kThreads) {
+    float v[kU];
+    uint64_t idx[kU];
+    bool on[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = j0 + u * kThreads;
+      on[u] = false;
+      idx[u] = 0;
+      v[u] = 0.0f;
+      if (j < n) {
+        const int c = k >> 4, e = k & 15;
+        const uint32_t m = s_m[c][pl];
+        on[u] = (m >> e) & 1u;
+        idx[u] = item_base + s_off[c][pl] + __popc(m & ((1u << e) - 1u));
+        if (mode == 0) v[u] = zb[j];
+        else if (on[u]) v[u] = packed[idx[u]];
+        pl += dpl;
+        k += dk;
+        if (k >= K) {
+          k -= K;
+          ++pl;
+        }
+      }
     }
-    pl += dpl;
-    k += dk;
-    if (k >= K) {
-      k -= K;
-      ++pl;
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = j0 + u * kThreads;
+      if (j >= n) break;
+      if (mode == 0) {
+        if (on[u]) packed[idx[u]] = v[u];
+      } else {
+        zb[j] = v[u];  // 0 off the sampled set (Eq. 4)
+      }
     }
   }
 }
