@@ -79,6 +79,16 @@ struct scsc_ctx {
   // screening: D^T r on the active set, per-filter tap prefix sums and norms,
   // per-image partials, per-image results and survivor counts
   DevBuf sg, spref, snrm, spart, simg, skept;
+  // the code step size (stencils + power iteration, ~160 launches) as one
+  // CUDA graph, captured once per key and replayed
+  struct StepKey {
+    const float *d;
+    int K, s, H, W;
+    const void *G, *A, *pu, *pw, *part, *scal, *prm;
+    double lambda;
+    uint64_t seed;
+  } step_key{};
+  cudaGraphExec_t step_exec = nullptr;
   // host-buffer entry: device copies of d and of two chunks of x and z, the
   // copy streams and the events that order them
   DevBuf hd, hx[2], hz[2];
@@ -312,16 +322,66 @@ scsc_status code_step_size(scsc_ctx *ctx, const float *d) {
     ctx->domainW = W;
   }
   const int sz = ctx->cfg.s;
+  const int64_t n = (int64_t)H * W;
   CK(ctx->ddtG.ensure((size_t)sz * sz * sz * sz * 8));
   CK(ctx->ddtA.ensure(ddt_stencil_floats(sz, H, W) * 4));
-  int pr = ctx->prof.begin(KID_POWER, ctx->stream);
-  CK(launch_ddt_prepare(d, ctx->cfg.K, sz, H, W, ctx->ddtG.as<double>(), ctx->ddtA.as<float>(),
-                        ctx->stream));
-  scsc_status s = power_iteration(
-      ctx, (int64_t)H * W, kTagLz, [&](const float *u, float *w) { return apply_ddt(ctx, u, w); },
-      0, prm, 0.0);
-  ctx->prof.end(pr, ctx->stream);
-  return s;
+  // every buffer of the power iteration exists before a capture starts
+  CK(ctx->pu.ensure((size_t)n * 4));
+  CK(ctx->pw.ensure((size_t)n * 4));
+  CK(ctx->partials.ensure((size_t)2 * kRedBlocks * 8));
+  cudaStream_t st = ctx->stream;
+  auto enqueue = [&]() -> scsc_status {
+    CK(launch_ddt_prepare(d, ctx->cfg.K, sz, H, W, ctx->ddtG.as<double>(), ctx->ddtA.as<float>(),
+                          st));
+    return power_iteration(
+        ctx, n, kTagLz, [&](const float *u, float *w) { return apply_ddt(ctx, u, w); }, 0, prm,
+        0.0);
+  };
+  int pr = ctx->prof.begin(KID_POWER, st);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cap));
+  const bool use_graph = st != nullptr && cap == cudaStreamCaptureStatusNone &&
+                         !(ctx->cfg.flags & SCSC_FLAG_NO_GRAPH);
+  scsc_status status = SCSC_OK;
+  if (!use_graph) {
+    status = enqueue();
+  } else {
+    scsc_ctx::StepKey key{};  // zero-filled, so that memcmp sees no padding bytes
+    key.d = d;
+    key.K = ctx->cfg.K;
+    key.s = sz;
+    key.H = H;
+    key.W = W;
+    key.G = ctx->ddtG.p;
+    key.A = ctx->ddtA.p;
+    key.pu = ctx->pu.p;
+    key.pw = ctx->pw.p;
+    key.part = ctx->partials.p;
+    key.scal = ctx->scal.p;
+    key.prm = prm;
+    key.lambda = ctx->cfg.lambda;
+    key.seed = ctx->cfg.seed;
+    if (!ctx->step_exec || std::memcmp(&key, &ctx->step_key, sizeof key) != 0) {
+      if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+      ctx->step_exec = nullptr;
+      CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      status = enqueue();
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamEndCapture(st, &g);
+      if (status != SCSC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return status;
+      }
+      CK(e);
+      e = cudaGraphInstantiate(&ctx->step_exec, g, 0);
+      cudaGraphDestroy(g);
+      CK(e);
+      ctx->step_key = key;
+    }
+    CK(cudaGraphLaunch(ctx->step_exec, st));
+  }
+  ctx->prof.end(pr, st);
+  return status;
 }
 
 scsc_status check_cfg(scsc_ctx *ctx, const scsc_config *c) {
@@ -376,8 +436,10 @@ scsc_status scsc_destroy(scsc_ctx *ctx) {
                     &ctx->gpart, &ctx->gsum, &ctx->pu, &ctx->pw,
                     &ctx->flag, &ctx->ddtG, &ctx->ddtA, &ctx->admm, &ctx->admm_partials,
                     &ctx->hd, &ctx->hx[0], &ctx->hx[1], &ctx->hz[0], &ctx->hz[1],
-                    &ctx->C, &ctx->B, &ctx->Cd, &ctx->batch.dev, &ctx->domain.dev})
+                    &ctx->C, &ctx->B, &ctx->Cd, &ctx->batch.dev, &ctx->domain.dev,
+                    &ctx->sg, &ctx->spref, &ctx->snrm, &ctx->spart, &ctx->simg, &ctx->skept})
     b->release();
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
   for (BatchCache *bc : {&ctx->batch, &ctx->domain}) {
     if (bc->pinned) cudaFreeHost(bc->pinned);
     if (bc->copied) cudaEventDestroy(bc->copied);
