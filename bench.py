@@ -387,7 +387,7 @@ def main():
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--per-image", action="store_true",
                     help="plain path: launch the kernels once per image (batched-launch baseline)")
     ap.add_argument("--no-autotune", action="store_true",
