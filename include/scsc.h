@@ -175,7 +175,8 @@ scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const fl
  *   R     = sqrt(2 (gap + 1e-6 (P + 0.5 ||x||^2))) / lambda,
  *   j leaves S when |g_j| / scale + R ||a_j|| < 1 - 1e-4,
  * ||a_j|| the norm of filter k over the taps that land on the image; the two
- * margins cover FP32 rounding.  Plain FP32 operators and FP64 reductions in
+ * margins cover FP32 rounding.  The data term is the plain one of Eq. 3
+ * (every pixel observed).  Plain FP32 operators and FP64 reductions in
  * either precision.  gap_host (n_images doubles, may be NULL): each image's
  * duality gap at the input codes; n_active_host (n_images int64, may be NULL):
  * the coordinates left in each image's set.  Synchronises the stream when an
