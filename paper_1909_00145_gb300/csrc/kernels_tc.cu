@@ -710,8 +710,9 @@ cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint8_t 
                         int max_smem, cudaStream_t st);
 cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
                         const uint64_t *seg_base, const uint16_t *pxoff, float *packed,
-                        uint8_t *abuf, const uint4 *badj, const float *r, const StepParams *prm,
-                        int *err, int grid, cudaStream_t st);
+                        uint8_t *abuf, const uint4 *badj, const float *xcore, const float *spill,
+                        const float *x, const uint8_t *obs, const StepParams *prm, int *err,
+                        int grid, cudaStream_t st);
 size_t tc_abuf_bytes(int K, int Q);
 cudaError_t prepare_pipe(int K, int s, int max_smem);
 
@@ -873,16 +874,26 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
       }));
     }
     if (ws.prof) ws.prof->end(p1, st);
-    int p2 = ws.prof ? ws.prof->begin(KID_FINALIZE, st) : -1;
-    finalize_r_kernel<<<fin_grid, kThreads, 0, st>>>(im, C, as<float>(ws.xcore), as<float>(ws.spill),
-                                                      x, obs, as<float>(ws.r));
-    TRY(cudaGetLastError());
-    if (ws.prof) ws.prof->end(p2, st);
+    // the pipelined adjoint forms the residual rows itself from xcore, the
+    // spill columns and x; with an observation mask (inpainting), and for
+    // the single-stage adjoint, r is formed here
+    if (v != 1 || obs != nullptr) {
+      int p2 = ws.prof ? ws.prof->begin(KID_FINALIZE, st) : -1;
+      finalize_r_kernel<<<fin_grid, kThreads, 0, st>>>(im, C, as<float>(ws.xcore),
+                                                        as<float>(ws.spill), x, obs, as<float>(ws.r));
+      TRY(cudaGetLastError());
+      if (ws.prof) ws.prof->end(p2, st);
+    }
     int p3 = ws.prof ? ws.prof->begin(KID_ADJ_TC, st) : -1;
     if (v == 1) {
-      TRY(launch_adj2(im, K, s, bits, seg_base, pxoff, as<float>(ws.packed),
-                      as<uint8_t>(ws.abuf), as<uint4>(ws.badj), as<float>(ws.r), prm,
-                      as<int>(ws.err), grid2, st));
+      if (obs == nullptr)
+        TRY(launch_adj2(im, K, s, bits, seg_base, pxoff, as<float>(ws.packed),
+                        as<uint8_t>(ws.abuf), as<uint4>(ws.badj), as<float>(ws.xcore),
+                        as<float>(ws.spill), x, nullptr, prm, as<int>(ws.err), grid2, st));
+      else
+        TRY(launch_adj2(im, K, s, bits, seg_base, pxoff, as<float>(ws.packed),
+                        as<uint8_t>(ws.abuf), as<uint4>(ws.badj), as<float>(ws.r), nullptr,
+                        nullptr, nullptr, prm, as<int>(ws.err), grid2, st));
     } else {
       TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
         constexpr int S = decltype(SC)::value;

@@ -120,7 +120,7 @@ struct Adj2 {
   __host__ __device__ static size_t mask_bytes(int KW) { return (size_t)kStrip * KW * 4; }
   __host__ __device__ static size_t total(int Kp, int KW) {
     return 1024 + b_bytes(Kp) + (size_t)RS * kSRow + 2 * vals_bytes(Kp) +
-           (size_t)kProd * 2 * 144 * 4;
+           (size_t)kProd * 4 * 144 * 4;
   }
 };
 
@@ -166,7 +166,10 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
                                                       float *__restrict__ packed,
                                                       uint8_t *__restrict__ abuf,
                                                       const uint4 *__restrict__ badj,
-                                                      const float *__restrict__ r,
+                                                      const float *__restrict__ xcore,
+                                                      const float *__restrict__ spill,
+                                                      const float *__restrict__ x,
+                                                      const uint8_t *__restrict__ obs,
                                                       const StepParams *__restrict__ prm,
                                                       int *err) {
   using L = Adj2<S>;
@@ -267,7 +270,12 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
   } else if (warp <= L::kProd) {
     // ------------------------------------------------ residual row producers
     const int pw = warp - 1;
-    float *const stg0 = rst + pw * 2 * 144, *const stg1 = stg0 + 144;
+    // staged rows of the synthesis output (stg) and of the image (sx), two
+    // each; with x == nullptr, xcore already holds the residual r and the rows
+    // are used as they arrive
+    const bool form_r = x != nullptr;
+    float *const stg0 = rst + pw * 4 * 144, *const stg1 = stg0 + 144;
+    float *const sx0 = stg0 + 2 * 144, *const sx1 = sx0 + 144;
     RowGen g;
     g.init(q_begin, q_end, C);
     // rows of this warp: sequence indices j = pw (mod kProd)
@@ -276,25 +284,27 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
         if ((int)(gg.j % L::kProd) == pw) return true;
       return false;
     };
-    auto issue = [&](const RowGen &gg, float *dst) {
+    auto issue = [&](const RowGen &gg, float *dst, float *dx) {
       const Item &it = gg.sg.it;
       const int ar = gg.ar(), b0 = it.js * kStrip;
       for (int k = lane; k < 144; k += 32) {
         const int col = b0 - C + k;
         const bool in = ar >= 0 && ar < it.H && col >= 0 && col < it.W;
-        tc::cp_async4(dst + k, in ? r + it.base + (int64_t)ar * it.W + col : r, in ? 4u : 0u);
+        const int64_t p = in ? it.base + (int64_t)ar * it.W + col : 0;
+        tc::cp_async4(dst + k, xcore + p, in ? 4u : 0u);
+        if (form_r) tc::cp_async4(dx + k, x + p, in ? 4u : 0u);
       }
       tc::cp_async_commit();
     };
     RowGen cur = g;
     bool have = next_mine(cur);
-    if (have) issue(cur, stg0);
+    if (have) issue(cur, stg0, sx0);
     int sbuf = 0;
     bool ok = true;
     while (have && ok) {
       RowGen nxt = cur;
       bool have_next = next_mine(nxt);
-      if (have_next) issue(nxt, sbuf ? stg0 : stg1);
+      if (have_next) issue(nxt, sbuf ? stg0 : stg1, sbuf ? sx0 : sx1);
       else tc::cp_async_commit();
       const int j = cur.j;
       const int slot = j & (RS - 1);
@@ -309,7 +319,42 @@ __global__ void __launch_bounds__(Adj2<S>::kThreads, 1) adj2_kernel(ItemMap im, 
       }
       tc::cp_async_wait<1>();
       __syncwarp();
-      const float *src0 = sbuf ? stg1 : stg0;
+      float *const src0 = sbuf ? stg1 : stg0;
+      if (form_r) {
+        // residual row ar: the synthesis's core columns plus the halo
+        // columns its neighbours spilled onto them (the left outer spill of
+        // this strip's item on k < c, the right outer spill of the left
+        // neighbour's item on c <= k < 2c, the left outer spill of the right
+        // neighbour's item on 128 <= k < 128 + c, this item's right outer
+        // spill beyond), minus the image; 0 off the image and at unobserved
+        // pixels
+        const float *const srcx = sbuf ? sx1 : sx0;
+        const Item &it = cur.sg.it;
+        const int ar = cur.ar(), b0 = it.js * kStrip;
+        const bool row_in = ar >= 0 && ar < it.H;
+        const int64_t qr = (int64_t)it.q_row0 + ar;
+        for (int k = lane; k < 144; k += 32) {
+          const int col = b0 - C + k;
+          float v = 0.0f;
+          if (row_in && col >= 0 && col < it.W) {
+            v = src0[k];
+            if (C > 0) {
+              if (k < C) v += spill[qr * (2 * C) + k];
+              else if (k < 2 * C) {
+                if (it.js > 0) v += spill[(qr - it.H) * (2 * C) + k];
+              } else if (k >= kStrip && k < kStrip + C) {
+                if (it.js + 1 < it.JS) v += spill[(qr + it.H) * (2 * C) + k - kStrip];
+              } else if (k >= kStrip + C && k < kStrip + 2 * C) {
+                v += spill[qr * (2 * C) + k - kStrip];
+              }
+            }
+            const int64_t p = it.base + (int64_t)ar * it.W + col;
+            v = (obs != nullptr && obs[p] == 0) ? 0.0f : v - srcx[k];
+          }
+          src0[k] = v;
+        }
+        __syncwarp();
+      }
       uint8_t *dst = ring + (size_t)slot * L::kSRow;
       for (int t2 = lane; t2 < 17 * 8; t2 += 32) {
         const int gq = t2 >> 3, ii = t2 & 7;
@@ -839,14 +884,16 @@ cudaError_t launch_syn2(const tcitems::ItemMap &im, int K, int s, const uint8_t 
 
 cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t *bits,
                         const uint64_t *seg_base, const uint16_t *pxoff, float *packed,
-                        uint8_t *abuf, const uint4 *badj, const float *r, const StepParams *prm,
-                        int *err, int grid, cudaStream_t st) {
+                        uint8_t *abuf, const uint4 *badj, const float *xcore, const float *spill,
+                        const float *x, const uint8_t *obs, const StepParams *prm, int *err,
+                        int grid, cudaStream_t st) {
   const int Kp = (K + 15) / 16 * 16, KW = (K + 31) / 32;
   return dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
     const size_t smem = Adj2<S>::total(Kp, KW);
     adj2_kernel<S><<<grid, Adj2<S>::kThreads, smem, st>>>(im, K, Kp, KW, bits, seg_base, pxoff,
-                                                          packed, abuf, badj, r, prm, err);
+                                                          packed, abuf, badj, xcore, spill, x,
+                                                          obs, prm, err);
     return cudaGetLastError();
   });
 }
