@@ -184,7 +184,8 @@ def launches_per_step(wl, path: str, n_iters: int, n_images: int, per_image: boo
     plain: apply-mask 1 + per iteration synthesis and adjoint (one launch per
     image with per_image) and the observed-pixel mask when there is one;
     tensor: filter images 1, segment counts 1, scan 3, pack 1, A tiles 1,
-    3 per iteration, unpack 1.  Screening adds 7 per test (apply-mask, tap
+    per iteration synthesis and adjoint (plus the residual pass with an
+    observation mask), unpack 1.  Screening adds 7 per test (apply-mask, tap
     norms, synthesis, adjoint, statistics, per-image finish, test).  ADMM:
     mask 1, init 1, A^T x 1, per iteration rhs 1, QP 3, CG init 1, dots 2,
     per CG step QP 3 + dots 2 + update 2, shrink 1; final 1."""
@@ -194,7 +195,7 @@ def launches_per_step(wl, path: str, n_iters: int, n_images: int, per_image: boo
         if path == "fp32":
             per_it = 2 * (n_images if per_image else 1) + (1 if obs else 0)
             return 1 + per_it * n
-        return 1 + 1 + 3 + 1 + 1 + 3 * n + 1
+        return 1 + 1 + 3 + 1 + 1 + (3 if obs else 2) * n + 1
 
     if wl.get("solver") == "admm":
         return 1 + 2 + n_iters * (1 + 3 + 1 + 2 + 7 * wl["cg_iters"] + 1) + 1
