@@ -26,7 +26,9 @@ def test_headers_declare_the_boundary():
     for need in ["scsc_create", "scsc_destroy", "scsc_code_step", "scsc_dict_step",
                  "scsc_objective", "scsc_mask", "scsc_synth", "scsc_synth_backward",
                  "scsc_lipschitz_codes", "scsc_last_error", "scsc_sync", "scsc_online_save",
-                 "scsc_online_load", "scsc_online_reset", "scsc_online_state_size"]:
+                 "scsc_online_load", "scsc_online_reset", "scsc_online_state_size",
+                 "scsc_code_step_host", "scsc_code_step_observed", "scsc_code_step_admm",
+                 "scsc_objective_observed", "scsc_screen", "scsc_code_step_screened"]:
         assert need in names
 
 
@@ -61,6 +63,13 @@ def test_null_context_is_rejected():
     assert L.scsc_destroy(None) == scsc.SCSC_OK
     assert L.scsc_sync(None) == scsc.SCSC_EINVAL
     assert L.scsc_code_step(None, None, None, None, None, 0, 1) == scsc.SCSC_EINVAL
+    assert L.scsc_code_step_host(None, None, None, None, None, 0, 1) == scsc.SCSC_EINVAL
+    assert L.scsc_code_step_observed(None, None, None, None, None, None, 0, 1) == scsc.SCSC_EINVAL
+    assert L.scsc_code_step_admm(None, None, None, None, None, 0, 1, 1, 0.0, 0.0) == \
+        scsc.SCSC_EINVAL
+    assert L.scsc_screen(None, None, None, None, None, None, None, None) == scsc.SCSC_EINVAL
+    assert L.scsc_code_step_screened(None, None, None, None, None, 0, 1, 1, None, None) == \
+        scsc.SCSC_EINVAL
 
 
 def test_batch_descriptor_layout():
