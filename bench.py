@@ -159,17 +159,27 @@ def peaks():
         return 6800.0, 1900.0, 1700.0, "fallback"
 
 
+def source_code_sha1(text: str) -> str:
+    """SHA-1 of a C++ source with its comments and whitespace runs removed:
+    unchanged as long as the code itself is."""
+    import hashlib
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    text = re.sub(r"\s+", " ", text).strip()
+    return hashlib.sha1(text.encode()).hexdigest()
+
+
 def measured_traffic(kernel: str, npx: int):
     """DRAM bytes per launch of `kernel` from the committed ncu counters of the
-    small profiling workload, scaled by pixels; None if the kernel source has
-    changed since the counters were taken."""
-    import hashlib
+    small profiling workload, scaled by pixels; None if the kernel source's
+    code has changed since the counters were taken."""
     names = {"adj_tc": "adj2_kernel", "synth_tc": "syn2_kernel"}
     try:
         with open(os.path.join(ROOT, "profiles", "tc_kernels_prof_workload_counters.json")) as f:
             c = json.load(f)
-        with open(os.path.join(ROOT, c["source"]), "rb") as f:
-            if hashlib.sha1(f.read()).hexdigest() != c["source_sha1"]:
+        with open(os.path.join(ROOT, c["source"])) as f:
+            if source_code_sha1(f.read()) != c["source_code_sha1"]:
                 return None
         k = c["kernels"][names[kernel]]
         return k["dram_bytes_per_launch"] * npx / c["workload_pixels"]

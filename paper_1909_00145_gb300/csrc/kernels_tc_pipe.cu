@@ -1,16 +1,18 @@
 // kernels_tc_pipe.cu -- warp-specialised, pipelined tcgen05 kernels of the
 // code update for K <= 128 (one persistent CTA per SM).
 //
-// Adjoint + prox (Eq. 3), 12 warps: warps 1-3 fetch residual rows with
-// cp.async and write each as 8 shifted BF16 copies (a Toeplitz view) into a
-// 16-slot shared-memory ring; warp 0 (lane 0) issues, per row item, one MMA
-// per tap row into one of two TMEM accumulators; warps 4-11 are two epilogue
-// groups of four warps (each covers all 128 pixels of the item and half of its
-// filter chunks): they prefetch the next item's packed codes with one bulk
-// copy and its mask words and pixel offsets into registers, apply the
-// soft-threshold step to the sampled coordinates, write the item back with
-// one bulk copy, and write the item's dense BF16 codes (zero off the sample)
-// in the synthesis's A-operand layout.
+// Adjoint + prox (Eq. 3), 13 warps: warps 1-3 form residual rows (the
+// synthesis output staged by cp.async, plus the neighbours' spill columns,
+// minus the image; or r itself when an observation mask applies) and write
+// each as 8 shifted BF16 copies (a Toeplitz view) into a 16-slot
+// shared-memory ring; warp 0 (lane 0) issues, per row item, one MMA per tap
+// row into one of two TMEM accumulators; warps 4-11 are two epilogue groups of
+// four warps (each covers all 128 pixels of the item and half of its units of
+// 8 filters), which run without block barriers: they apply the soft-threshold
+// step to the sampled coordinates of the staged packed codes and write the
+// item's dense BF16 codes (zero off the sample) in the synthesis's A-operand
+// layout; warp 12 (lane 0) stages each item's packed codes by one bulk copy
+// and writes them back by another once every epilogue warp is done.
 //
 // Synthesis, 5 warps: warp 4 (lane 0) fetches each code row's dense BF16 A
 // tile by one bulk copy (up to 4 rows ahead) and issues the MMAs P = Z D^T
