@@ -232,6 +232,17 @@ def test_code_step_bf16_large_k_fallback_kernels():
     assert fg == pytest.approx(fo, rel=1e-3)
 
 
+@pytest.mark.parametrize("K", [128, 113, 1])
+def test_code_step_pipelined_limits(K):
+    """The pipelined kernels at their limits: Kp = 128 with 11 x 11 filters and
+    every coordinate sampled (the largest shared-memory layout and full items),
+    and a single filter."""
+    zg, zo, fg, fo, _ = run_code_step("bf16", K, 11, [40, 30], [140, 70], (1, 1), 5, seed=12,
+                                      lam=0.8)
+    assert fg == pytest.approx(fo, rel=1e-3)
+    assert rel_l2(zg, zo) < 5e-2
+
+
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_code_step_many_items_per_cta(prec):
     """A batch with many more 128-pixel row items than SMs, so that each
