@@ -41,7 +41,7 @@ typedef enum {
   SCSC_ECUDA = 3,        /* a CUDA runtime call or a kernel launch failed  */
   SCSC_ETIMEOUT = 4,     /* a bounded device-side wait ran out             */
   SCSC_ENONFINITE = 5,   /* NaN/Inf found in an input                      */
-  SCSC_EUNSUPPORTED = 6  /* valid request that this build does not support */
+  SCSC_EUNSUPPORTED = 6  /* valid request that the library does not support */
 } scsc_status;
 
 typedef enum {
