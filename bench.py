@@ -542,7 +542,9 @@ def main():
         avg_s = kt[dom][0] / (kt[dom][1] / per_iter) / 1e3
         # algorithmic bytes per launch (stated per kernel in the design notes)
         bytes_per_launch = {
-            "adj_tc": 8 * sampled + 4 * kw * npx + 4 * npx,       # packed r+w, mask, residual
+            # packed r+w, mask, and the residual: r itself with an observation
+            # mask, else the synthesis output and the image it is formed from
+            "adj_tc": 8 * sampled + 4 * kw * npx + (4 if obs is not None else 8) * npx,
             "synth_tc": 4 * sampled + 4 * kw * npx + 4 * npx,     # packed read, mask, xhat write
             "adjoint_fp32": 8 * sampled + 4 * kw * npx + 4 * npx,
             "synth_fp32": 4 * npx * K + 8 * npx,
