@@ -24,13 +24,23 @@ extern "C" {
 
 scsc_status scsc_diag_tc_gemm(int N, const float *A_dev, const float *B_dev, float *D_dev);
 
+/* scsc_diag_wait_timeout launches one block whose thread waits on a
+ * shared-memory mbarrier that nothing arrives on, through the bounded wait
+ * every tensor kernel uses, with a limit of limit_ms milliseconds (0 <
+ * limit_ms <= 1000).  The wait gives up at the limit and raises the kernel's
+ * error word, which the host reads.  Returns SCSC_ETIMEOUT when the wait ran
+ * out (the expected outcome), SCSC_OK if it did not, SCSC_EINVAL for a bad
+ * limit, SCSC_ENOMEM / SCSC_ECUDA as scsc_diag_tc_gemm.  Runs on the legacy
+ * default stream and synchronises the device; the context stays usable. */
+scsc_status scsc_diag_wait_timeout(double limit_ms);
+
 /* Per-kernel timing.  scsc_diag_profile(ctx, 1) synchronises the context's
  * stream, clears the records and from then on brackets every launch of the
  * library's kernels with a pair of CUDA events on that stream; 0 turns it
  * off.  scsc_diag_kernel_time() waits for the recorded events and returns the
  * summed device time and the launch count of one kernel, named "mask",
  * "power", "synth_fp32", "adjoint_fp32", "pack", "synth_tc", "finalize_r",
- * "adj_tc" or "unpack" (SCSC_EINVAL for another name). */
+ * "adj_tc", "unpack" or "screen" (SCSC_EINVAL for another name). */
 scsc_status scsc_diag_profile(scsc_ctx *ctx, int enable);
 scsc_status scsc_diag_kernel_time(scsc_ctx *ctx, const char *name, double *total_ms,
                                   int *launches);

@@ -1014,6 +1014,25 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   return cudaSuccess;
 }
 
+namespace {
+// A bounded wait on an mbarrier that nothing arrives on: the wait gives up
+// after limit_ns, as every wait of the tensor kernels does, and raises the
+// error word (one thread, one block).
+__global__ void selftest_wait_kernel(uint64_t limit_ns, int *err) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_mbar_init();
+    if (!tc::mbar_wait_bounded(&bar, 0, limit_ns)) atomicExch(err, 1);
+  }
+}
+}  // namespace
+
+cudaError_t tc_selftest_wait(uint64_t limit_ns, int *err, cudaStream_t st) {
+  selftest_wait_kernel<<<1, 32, 0, st>>>(limit_ns, err);
+  return cudaGetLastError();
+}
+
 cudaError_t tc_selftest_gemm(int N, const float *A, const float *B, float *D, int *err,
                              cudaStream_t st) {
   if (N < 16 || N > 256 || N % 16 != 0) return cudaErrorInvalidValue;

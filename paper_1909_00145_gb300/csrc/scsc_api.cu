@@ -982,6 +982,24 @@ scsc_status scsc_diag_tc_gemm(int N, const float *A_dev, const float *B_dev, flo
   return s;
 }
 
+scsc_status scsc_diag_wait_timeout(double limit_ms) {
+  if (!(limit_ms > 0.0 && limit_ms <= 1000.0)) return SCSC_EINVAL;
+  int *err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return SCSC_ENOMEM;
+  scsc_status s = SCSC_OK;
+  if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
+      tc_selftest_wait((uint64_t)(limit_ms * 1e6), err, nullptr) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    s = SCSC_ECUDA;
+  } else {
+    int word = 0;
+    if (cudaMemcpy(&word, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) s = SCSC_ECUDA;
+    else if (word) s = SCSC_ETIMEOUT;
+  }
+  cudaFree(err);
+  return s;
+}
+
 scsc_status scsc_online_reset(scsc_ctx *ctx) {
   if (!ctx) return SCSC_EINVAL;
   ctx->online_t = 0;

@@ -80,6 +80,8 @@ const char *tc_last_error(const TcWorkspace &ws);
 // operands rounded from the float inputs, FP32 accumulation); device buffers.
 cudaError_t tc_selftest_gemm(int N, const float *A, const float *B, float *D, int *err,
                              cudaStream_t st);
+// One bounded mbarrier wait that nothing completes: sets *err after limit_ns.
+cudaError_t tc_selftest_wait(uint64_t limit_ns, int *err, cudaStream_t st);
 
 // Pipelined tensor kernels (kernels_tc_pipe.cu): K <= 128 and shared memory
 // within `max_smem` bytes per block.

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "scsc_online_save": [c_void_p, c_void_p, c_size_t],
     "scsc_online_load": [c_void_p, c_void_p, c_size_t],
     "scsc_diag_tc_gemm": [c_int, c_void_p, c_void_p, c_void_p],
+    "scsc_diag_wait_timeout": [c_double],
     "scsc_objective_noalloc": [ctypes.POINTER(scsc_config), c_int, c_int, c_int, c_void_p,
                                c_void_p, c_void_p, c_void_p, c_void_p],
     "scsc_diag_profile": [c_void_p, c_int],
