@@ -179,7 +179,6 @@ extern "C" scsc_status scsc_objective_noalloc(const scsc_config *cfg, int n_imag
   if (st != SCSC_OK) return st;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   const int64_t npx = (int64_t)n_images * H * W;
-  cudaError_t e = cudaSuccess;
   switch (s) {
 #define SCSC_CASE(SV)                                                                        \
   case SV:                                                                                   \
@@ -195,10 +194,10 @@ extern "C" scsc_status scsc_objective_noalloc(const scsc_config *cfg, int n_imag
 #undef SCSC_CASE
     default: return SCSC_EINVAL;
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return SCSC_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return SCSC_ECUDA;
   abs_sum_kernel<<<kAbsBlocks, 256, 0, stream>>>(z_dev, npx * K, part + kMaxTiles);
-  if ((e = cudaGetLastError()) != cudaSuccess) return SCSC_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return SCSC_ECUDA;
   finish_kernel<<<1, 256, 0, stream>>>(part, (int)tiles, cfg->lambda, out_dev);
-  if ((e = cudaGetLastError()) != cudaSuccess) return SCSC_ECUDA;
+  if (cudaGetLastError() != cudaSuccess) return SCSC_ECUDA;
   return SCSC_OK;
 }
