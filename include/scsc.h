@@ -157,7 +157,8 @@ scsc_status scsc_code_step_observed(scsc_ctx *ctx, const scsc_batch *batch, cons
  * out: y on the sampled set, zero elsewhere (Eq. 4).  rho <= 0 selects the
  * paper's 10 lambda, alpha <= 0 its 1.8 (alpha must be < 2).  Plain FP32
  * operators, FP64 CG reductions, for every precision setting.  Errors as
- * scsc_code_step; SCSC_EINVAL for n_iters or cg_iters < 0. */
+ * scsc_code_step; SCSC_EINVAL for n_iters or cg_iters < 0 and for batches of more
+ * than 65535 images. */
 scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
                                 const float *d_dev, float *z_dev, uint64_t t, int n_iters,
                                 int cg_iters, double rho, double alpha);
@@ -180,7 +181,8 @@ scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const fl
  * either precision.  gap_host (n_images doubles, may be NULL): each image's
  * duality gap at the input codes; n_active_host (n_images int64, may be NULL):
  * the coordinates left in each image's set.  Synchronises the stream when an
- * output is requested.  Errors as scsc_code_step. */
+ * output is requested.  Errors as scsc_code_step; SCSC_EINVAL for batches of
+ * more than 65535 images. */
 scsc_status scsc_screen(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
                         const float *d_dev, float *z_dev, uint32_t *bits_dev, double *gap_host,
                         int64_t *n_active_host);
@@ -190,7 +192,8 @@ scsc_status scsc_screen(scsc_ctx *ctx, const scsc_batch *batch, const float *x_d
  * M^t, before iterations 0, e, 2e, ... (e = screen_every >= 1); the iterations
  * update the active coordinates only, and the removed ones stay zero.  The
  * outputs are those of the last test (SCSC_EINVAL if one is requested with
- * n_iters = 0).  SCSC_EINVAL for n_iters < 0 or screen_every < 1. */
+ * n_iters = 0).  SCSC_EINVAL for n_iters < 0, screen_every < 1 or more than
+ * 65535 images. */
 scsc_status scsc_code_step_screened(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
                                     const float *d_dev, float *z_dev, uint64_t t, int n_iters,
                                     int screen_every, double *gap_host, int64_t *n_active_host);

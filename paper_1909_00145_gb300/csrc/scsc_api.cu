@@ -28,6 +28,9 @@ constexpr uint64_t kTagLz = 0x4C;      // start-vector tags of the three power i
 constexpr uint64_t kTagLd = 0x44;
 constexpr uint64_t kTagLc = 0x43;
 constexpr int kRedBlocks = 1024;       // blocks of the FP64 reductions (fixed: deterministic)
+// The ADMM and screening kernels launch one grid row per image (grid y, at
+// most 65535).
+constexpr int kMaxGridImages = 65535;
 constexpr int kGradGroups = 304;       // block rows of the filter-gradient reduction (2 x 152 SMs)
 constexpr uint32_t kStateMagic = 0x43534353u;  // "SCSC"
 
@@ -674,6 +677,8 @@ scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const fl
     return fail(ctx, SCSC_EINVAL, "rho = %g, alpha = %g outside rho > 0, 0 < alpha < 2", rho,
                 alpha_r);
   CKS(stage_batch(ctx, batch));
+  if (ctx->batch.view.n > kMaxGridImages)
+    return fail(ctx, SCSC_EINVAL, "ADMM: at most %d images per call", kMaxGridImages);
   CKS(build_mask(ctx, t));
   const BatchDev &b = ctx->batch.view;
   const int K = ctx->cfg.K, s = ctx->cfg.s;
@@ -786,6 +791,8 @@ scsc_status scsc_screen(scsc_ctx *ctx, const scsc_batch *batch, const float *x_d
   if (!ctx) return SCSC_EINVAL;
   if (!x_dev || !d_dev || !z_dev || !bits_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
   CKS(stage_batch(ctx, batch));
+  if (ctx->batch.view.n > kMaxGridImages)
+    return fail(ctx, SCSC_EINVAL, "screening: at most %d images per call", kMaxGridImages);
   CKS(screen_enqueue(ctx, x_dev, d_dev, z_dev, bits_dev));
   return screen_outputs(ctx, gap_host, n_active_host);
 }
@@ -798,6 +805,8 @@ scsc_status scsc_code_step_screened(scsc_ctx *ctx, const scsc_batch *batch, cons
   if (n_iters < 0) return fail(ctx, SCSC_EINVAL, "n_iters = %d < 0", n_iters);
   if (screen_every < 1) return fail(ctx, SCSC_EINVAL, "screen_every = %d < 1", screen_every);
   CKS(stage_batch(ctx, batch));
+  if (ctx->batch.view.n > kMaxGridImages)
+    return fail(ctx, SCSC_EINVAL, "screening: at most %d images per call", kMaxGridImages);
   CKS(build_mask(ctx, t));
   CKS(code_step_size(ctx, d_dev));
   uint32_t *bits = ctx->bits.as<uint32_t>();
