@@ -423,6 +423,12 @@ def scsc_diag_tc_gemm(A, B):
     return D
 
 
+def scsc_diag_wait_timeout(limit_ms: float = 20.0) -> int:
+    """Run the kernels' bounded mbarrier wait on a barrier that nothing
+    completes; returns the status (SCSC_ETIMEOUT when the wait ran out)."""
+    return int(lib().scsc_diag_wait_timeout(float(limit_ms)))
+
+
 def scsc_diag_profile(ctx: Context, enable: bool = True) -> None:
     _check(lib().scsc_diag_profile(ctx.handle, int(enable)), ctx.handle, "scsc_diag_profile")
 
