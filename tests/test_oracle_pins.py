@@ -582,3 +582,33 @@ def test_screened_code_step_reaches_the_unscreened_optimum():
     assert np.all(active[z_plain != 0] == 1)
     assert active.sum() < m.sum() and np.all(active <= m)
     assert gaps[0] >= 0.0
+
+
+@pytest.mark.parametrize("seed", [101, 202, 303, 404])
+def test_screening_safety_on_random_small_problems(seed):
+    """Safety over random shapes, filters, sampling rates and lambdas: at
+    random iterates (including random codes off the optimum), no coordinate
+    the test removes is nonzero in the solution (2·10^4 PG iterations)."""
+    g = np.random.default_rng(seed)
+    K, s = int(g.integers(2, 4)), int(g.choice([3, 5]))
+    H, W = int(g.integers(6, 11)), int(g.integers(6, 11))
+    d = I.filters(seed, K, s).astype(np.float64)
+    x = I.images(seed + 1, [H], [W]).astype(np.float64)
+    p_den = int(g.choice([1, 2, 3]))
+    base = R.Config(K=K, s=s, lam=1.0, p_num=1, p_den=p_den, seed=seed)
+    m = R.mask_image(base, 1, 0, H, W).ravel()
+    A = explicit_synthesis_matrix(d.reshape(K, s, s), H, W)
+    lam_max = float(np.abs(A[:, m == 1].T @ x).max())
+    cfg = R.Config(K=K, s=s, lam=float(g.uniform(0.2, 0.95)) * lam_max, p_num=1, p_den=p_den,
+                   seed=seed)
+    batch = R.Batch(H=[H], W=[W], ids=[0])
+    z_star = R.code_step(cfg, batch, x, d, np.zeros(m.size), t=1, n_iters=20000)
+    zeros = (m == 1) & (z_star == 0)
+    starts = [R.code_step(cfg, batch, x, d, np.zeros(m.size), t=1, n_iters=int(n))
+              for n in g.integers(0, 400, size=3)]
+    starts.append(g.normal(scale=0.1, size=m.size) * m)
+    for z0 in starts:
+        _, mm, gap, _ = R.screen_image(cfg, d, x, z0, m, H, W)
+        removed = (m == 1) & (mm == 0)
+        assert gap >= 0.0
+        assert not np.any(removed & ~zeros)
