@@ -136,6 +136,28 @@ def _ptr(t) -> int:
     return t.data_ptr()
 
 
+def _need(t, n: int, esize: int, name: str) -> None:
+    """The C entry points take raw pointers: check here that a tensor holds at
+    least n elements of esize bytes, so that no kernel runs past its end."""
+    if t is None:
+        return
+    if t.element_size() != esize:
+        raise ValueError(f"{name}: expected {esize}-byte elements, got {t.element_size()}")
+    if t.numel() < n:
+        raise ValueError(f"{name}: {t.numel()} elements, the batch needs {n}")
+
+
+def _need_step(ctx, batch, x=None, d=None, z=None, observed=None, bits=None) -> None:
+    """Sizes of the batch-level arguments: x and observed one per pixel, z K
+    per pixel, d K s s, bits ceil(K/32) words per pixel."""
+    P, K = batch.total_pixels, ctx.K
+    _need(x, P, 4, "x")
+    _need(d, K * ctx.s * ctx.s, 4, "d")
+    _need(z, P * K, 4, "z")
+    _need(observed, P, 1, "observed")
+    _need(bits, P * ((K + 31) // 32), 4, "bits")
+
+
 class Batch:
     """Host descriptor of images packed back to back (scsc_batch)."""
 
@@ -262,17 +284,20 @@ def scsc_mask(ctx: Context, batch: Batch, t: int):
 
 
 def scsc_code_step(ctx: Context, batch: Batch, x, d, z, t: int, n_iters: int) -> None:
+    _need_step(ctx, batch, x=x, d=d, z=z)
     _check(lib().scsc_code_step(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d), _ptr(z), t,
                                 n_iters), ctx.handle, "scsc_code_step")
 
 
 def scsc_dict_step(ctx: Context, batch: Batch, x, z, d, mode: int = SCSC_DICT_BATCH,
                    t: int = 1) -> None:
+    _need_step(ctx, batch, x=x, d=d, z=z)
     _check(lib().scsc_dict_step(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(z), _ptr(d),
                                 mode, t), ctx.handle, "scsc_dict_step")
 
 
 def scsc_objective(ctx: Context, batch: Batch, x, z, d) -> float:
+    _need_step(ctx, batch, x=x, d=d, z=z)
     out = c_double()
     _check(lib().scsc_objective(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(z), _ptr(d),
                                 ctypes.byref(out)), ctx.handle, "scsc_objective")
@@ -283,6 +308,7 @@ def scsc_code_step_observed(ctx: Context, batch: Batch, x, d, z, observed, t: in
                             n_iters: int) -> None:
     """Inpainting code update: observed is a uint8 device tensor, one byte per
     pixel (nonzero = observed), or None for every pixel."""
+    _need_step(ctx, batch, x=x, d=d, z=z, observed=observed)
     _check(lib().scsc_code_step_observed(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d),
                                          _ptr(z), _ptr(observed) if observed is not None else None,
                                          t, n_iters), ctx.handle, "scsc_code_step_observed")
@@ -297,6 +323,7 @@ def _host_ptr(t) -> int:
 
 def scsc_code_step_host(ctx: Context, batch: Batch, x, d, z, t: int, n_iters: int) -> None:
     """scsc_code_step on host (CPU) tensors; z is updated in place."""
+    _need_step(ctx, batch, x=x, d=d, z=z)
     _check(lib().scsc_code_step_host(ctx.handle, ctypes.byref(batch.c), _host_ptr(x),
                                      _host_ptr(d), _host_ptr(z), t, n_iters), ctx.handle,
            "scsc_code_step_host")
@@ -305,6 +332,7 @@ def scsc_code_step_host(ctx: Context, batch: Batch, x, d, z, t: int, n_iters: in
 def scsc_code_step_admm(ctx: Context, batch: Batch, x, d, z, t: int, n_iters: int,
                         cg_iters: int, rho: float = 0.0, alpha: float = 0.0) -> None:
     """ADMM code update (rho, alpha <= 0: the paper's 10 lambda and 1.8)."""
+    _need_step(ctx, batch, x=x, d=d, z=z)
     _check(lib().scsc_code_step_admm(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d), _ptr(z),
                                      t, n_iters, cg_iters, float(rho), float(alpha)), ctx.handle,
            "scsc_code_step_admm")
@@ -315,6 +343,7 @@ def scsc_screen(ctx: Context, batch: Batch, x, d, z, bits):
     the scsc_mask layout; updated in place, as are the codes z).  Returns
     (per-image duality gaps, per-image active counts) as numpy arrays."""
     import numpy as np
+    _need_step(ctx, batch, x=x, d=d, z=z, bits=bits)
     gaps = np.zeros(batch.n, dtype=np.float64)
     kept = np.zeros(batch.n, dtype=np.int64)
     _check(lib().scsc_screen(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d), _ptr(z),
@@ -328,6 +357,7 @@ def scsc_code_step_screened(ctx: Context, batch: Batch, x, d, z, t: int, n_iters
     """Code step with the screening test every `screen_every` iterations.
     Returns (per-image gaps, per-image active counts) of the last test."""
     import numpy as np
+    _need_step(ctx, batch, x=x, d=d, z=z)
     gaps = np.zeros(batch.n, dtype=np.float64)
     kept = np.zeros(batch.n, dtype=np.int64)
     _check(lib().scsc_code_step_screened(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(d),
@@ -339,6 +369,7 @@ def scsc_code_step_screened(ctx: Context, batch: Batch, x, d, z, t: int, n_iters
 
 
 def scsc_objective_observed(ctx: Context, batch: Batch, x, z, d, observed) -> float:
+    _need_step(ctx, batch, x=x, d=d, z=z, observed=observed)
     out = c_double()
     _check(lib().scsc_objective_observed(ctx.handle, ctypes.byref(batch.c), _ptr(x), _ptr(z),
                                          _ptr(d),
@@ -348,6 +379,7 @@ def scsc_objective_observed(ctx: Context, batch: Batch, x, z, d, observed) -> fl
 
 
 def scsc_lipschitz_codes(ctx: Context, batch: Batch, d) -> float:
+    _need_step(ctx, batch, d=d)
     out = c_double()
     _check(lib().scsc_lipschitz_codes(ctx.handle, ctypes.byref(batch.c), _ptr(d),
                                       ctypes.byref(out)), ctx.handle, "scsc_lipschitz_codes")
@@ -358,6 +390,7 @@ def scsc_synth(ctx: Context, batch: Batch, z, d, t: int = 0, masked: bool = Fals
     import torch
     if out is None:
         out = torch.empty(batch.total_pixels, dtype=torch.float32, device=z.device)
+    _need_step(ctx, batch, x=out, d=d, z=z)
     _check(lib().scsc_synth(ctx.handle, ctypes.byref(batch.c), _ptr(z), _ptr(d), t, int(masked),
                             _ptr(out)), ctx.handle, "scsc_synth")
     return out
@@ -368,6 +401,7 @@ def scsc_synth_backward(ctx: Context, batch: Batch, grad, z, d, t: int = 0, mask
     import torch
     gz = torch.empty(batch.total_pixels * ctx.K, dtype=torch.float32, device=grad.device) if need_z else None
     gd = torch.empty(ctx.K * ctx.s * ctx.s, dtype=torch.float32, device=grad.device) if need_d else None
+    _need_step(ctx, batch, x=grad, d=d, z=z)
     _check(lib().scsc_synth_backward(ctx.handle, ctypes.byref(batch.c), _ptr(grad), _ptr(z),
                                      _ptr(d), t, int(masked), _ptr(gz), _ptr(gd)), ctx.handle,
            "scsc_synth_backward")

@@ -77,3 +77,22 @@ def test_batch_descriptor_layout():
     assert list(b.offsets) == [0, 12]
     assert b.total_pixels == 22
     assert ctypes.sizeof(scsc.scsc_config) == 56
+
+
+def test_binding_checks_buffer_sizes_before_any_launch():
+    torch = pytest.importorskip("torch")
+
+    class Ctx:
+        K, s = 20, 5
+
+    b = scsc.Batch([3, 5], [4, 2])  # 22 pixels
+    ok = dict(x=torch.zeros(22), d=torch.zeros(20 * 25), z=torch.zeros(22 * 20),
+              observed=torch.zeros(22, dtype=torch.uint8), bits=torch.zeros(22, dtype=torch.int32))
+    scsc._need_step(Ctx, b, **ok)
+    scsc._need_step(Ctx, b, x=torch.zeros(40))  # larger is fine
+    for name, bad in [("x", torch.zeros(21)), ("d", torch.zeros(20 * 25 - 1)),
+                      ("z", torch.zeros(22 * 20 - 1)), ("observed", torch.zeros(22)),
+                      ("bits", torch.zeros(21, dtype=torch.int32)),
+                      ("x", torch.zeros(22, dtype=torch.float64))]:
+        with pytest.raises(ValueError, match=name):
+            scsc._need_step(Ctx, b, **{name: bad})
