@@ -260,7 +260,10 @@ scsc_status scsc_sync(scsc_ctx *ctx);
  * 32 x 32 pixels (n_images * ceil(H/32) * ceil(W/32) <= 65,536); larger
  * batches are rejected with SCSC_EINVAL before anything is launched.
  * The first call on a device looks up the array's device address with that
- * device current; make that first call outside any stream capture.  All
+ * device current; make that first call outside any stream capture.  The
+ * address is cached with the id of the device's current CUDA context and
+ * looked up again when that context changes (after cudaDeviceReset), so a
+ * call after a reset is again a first call.  All
  * calls share the array and each call overwrites what it reads, so calls
  * that overlap on the GPU (on different streams or devices sharing nothing
  * else) race and must be serialised by the caller. */

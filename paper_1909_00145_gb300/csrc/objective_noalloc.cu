@@ -27,7 +27,15 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_scratch[kMaxTiles + kAbsBlocks];
 
 std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {};
+// Cached address of g_scratch per device, with the id of the CUDA context it
+// was looked up in: a device reset (or any new primary context) reloads the
+// module, so an address from an older context is stale and is looked up anew.
+struct ScratchSlot {
+  double *ptr = nullptr;
+  unsigned long long ctx_id = 0;
+  bool have_id = false;
+};
+ScratchSlot g_slot[kMaxDevices];
 
 // Per-tile sum of (D z - x)^2 over one 32x32 tile of image n = tile / tiles_per_image.
 template <int S>
@@ -144,19 +152,57 @@ __global__ void finish_kernel(const double *__restrict__ part, int n_tiles, doub
   }
 }
 
-// Address of the scratch array on the current device, looked up once per
-// device (cudaGetSymbolAddress with that device current).
+// Id of the CUDA context current on this thread (driver entry points fetched
+// through the runtime, so the library does not link the driver library).
+// False when no context is current or the entry points are unavailable.
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+bool current_context_id(unsigned long long *id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void *f1 = nullptr, *f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess &&
+        q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess &&
+        q2 == cudaDriverEntryPointSuccess) {
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f1);
+      get_id = reinterpret_cast<CtxGetIdFn>(f2);
+    }
+    looked_up = true;
+  }
+  if (!get_current || !get_id) return false;
+  void *ctx = nullptr;
+  if (get_current(&ctx) != 0 || ctx == nullptr) return false;
+  return get_id(ctx, id) == 0;
+}
+
+// Address of the scratch array on the current device.  Looked up with that
+// device current on the first call, and again whenever the device's current
+// context is not the one of the cached address (after a device reset), or on
+// every call where the context id cannot be read.
 scsc_status scratch_for_current_device(double **ptr) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SCSC_ECUDA;
   if (dev < 0 || dev >= kMaxDevices) return SCSC_EUNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_scratch_ptr[dev] == nullptr) {
+  ScratchSlot &slot = g_slot[dev];
+  unsigned long long id = 0;
+  bool have_id = current_context_id(&id);
+  if (slot.ptr == nullptr || !have_id || !slot.have_id || slot.ctx_id != id) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return SCSC_ECUDA;
-    g_scratch_ptr[dev] = static_cast<double *>(p);
+    // the lookup makes the device's primary context current if none was
+    if (!have_id) have_id = current_context_id(&id);
+    slot.ptr = static_cast<double *>(p);
+    slot.ctx_id = id;
+    slot.have_id = have_id;
   }
-  *ptr = g_scratch_ptr[dev];
+  *ptr = slot.ptr;
   return SCSC_OK;
 }
 

@@ -411,7 +411,18 @@ def scsc_synth_backward(ctx: Context, batch: Batch, grad, z, d, t: int = 0, mask
 def scsc_objective_noalloc(K: int, s: int, lam: float, n_images: int, H: int, W: int, x, z, d,
                            out, stream=None) -> None:
     """Eq. 1 for equal-size images into the device double `out`, using only the
-    library's built-in scratch (no device allocation)."""
+    library's built-in scratch (no device allocation).  Buffer sizes and
+    element types are checked here, before the library is touched: the C
+    entry point takes raw pointers and cannot see a short or wrongly typed
+    tensor."""
+    P = int(n_images) * int(H) * int(W)
+    for name, t, n, fp in (("x", x, P, 4), ("z", z, P * int(K), 4),
+                           ("d", d, int(K) * int(s) * int(s), 4), ("out", out, 1, 8)):
+        if t is None:
+            raise ValueError(f"{name}: a tensor is required")
+        if not t.is_floating_point():
+            raise ValueError(f"{name}: expected a float{8 * fp} tensor, got {t.dtype}")
+        _need(t, n, fp, name)
     cfg = scsc_config(int(K), int(s), float(lam), 1, 1, 0, SCSC_FP32, 0.0, 0)
     _check(lib().scsc_objective_noalloc(ctypes.byref(cfg), n_images, H, W, _ptr(x), _ptr(z),
                                         _ptr(d), _ptr(out), c_void_p(_stream_handle(stream))),

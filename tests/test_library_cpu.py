@@ -96,3 +96,30 @@ def test_binding_checks_buffer_sizes_before_any_launch():
                       ("x", torch.zeros(22, dtype=torch.float64))]:
         with pytest.raises(ValueError, match=name):
             scsc._need_step(Ctx, b, **{name: bad})
+
+
+def test_objective_noalloc_binding_checks_buffers_before_any_launch():
+    # short or wrongly typed buffers are rejected by the binding before the
+    # library is called (CPU tensors: nothing could be launched on them)
+    torch = pytest.importorskip("torch")
+    K, s, n, H, W = 4, 3, 2, 8, 8
+    P = n * H * W
+    x = torch.zeros(P)
+    z = torch.zeros(P * K)
+    d = torch.zeros(K * s * s)
+    out = torch.zeros(1, dtype=torch.float64)
+    bad = [
+        dict(z=torch.zeros(P)),                          # n H W values instead of n H W K
+        dict(x=torch.zeros(P, dtype=torch.float64)),     # float64 image
+        dict(z=torch.zeros(P * K, dtype=torch.float64)),
+        dict(d=torch.zeros(K * s * s - 1)),
+        dict(out=torch.zeros(1, dtype=torch.float32)),   # the result is one double
+        dict(x=torch.zeros(P, dtype=torch.int32)),       # right size, not a float
+        dict(x=None),
+    ]
+    for kw in bad:
+        args = dict(x=x, z=z, d=d, out=out)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            scsc.scsc_objective_noalloc(K, s, 1.0, n, H, W, args["x"], args["z"], args["d"],
+                                        args["out"])
