@@ -60,6 +60,22 @@ def test_splitmix64_published_vectors():
         assert R.splitmix64(int(inp, 16)) == int(out, 16)
 
 
+def test_mask_key_order_golden_value():
+    """The hash chain's key order (seed, then t, then n, then the coordinate
+    index) and the strict threshold test, against a value derived from the
+    published SplitMix64 vectors (derivation in the fixture)."""
+    kv = dict(l.split() for l in open(os.path.join(GOLDEN, "mask_key_order.txt"))
+              if l.strip() and not l.startswith("#"))
+    seed, t, n = int(kv["seed"], 16), int(kv["t"], 16), int(kv["n"], 16)
+    H, W, k, y, x = (int(kv[c]) for c in "HWkyx")
+    hi = int(kv["hash"], 16) >> 32
+    K = 2
+    for p_num, want in ((hi, 0), (hi + 1, 1)):
+        cfg = R.Config(K=K, p_num=p_num, p_den=2**32 - 1, seed=seed)
+        m = R.mask_image(cfg, t, n, H, W)
+        assert m[y, x, k] == want, (p_num, want)
+
+
 def test_mask_p_one_is_identity_and_p_zero_is_empty():
     # Sec. 3.1: p = 1 makes M^t the identity.
     full = R.mask_image(R.Config(K=7, p_num=1, p_den=1, seed=5), 3, 11, 9, 13)
