@@ -23,6 +23,14 @@
  * thread-safe.  Errors are returned as scsc_status codes; argument errors are
  * found on the host before anything is launched, and scsc_last_error() holds
  * a one-line description.  Device code never traps.
+ *
+ * Inputs are checked for NaN and infinities on the device, without a trap:
+ * every call that reads x, z or d (or a gradient) enqueues a check that sets a
+ * flag word of the context, and the next synchronising call (scsc_sync,
+ * scsc_objective, scsc_objective_observed, scsc_lipschitz_codes,
+ * scsc_code_step_host) returns SCSC_ENONFINITE and clears the word when it
+ * was set.  The outputs of the calls since the previous report are then
+ * undefined; the context stays usable.
  */
 #ifndef SCSC_H
 #define SCSC_H
@@ -46,8 +54,11 @@ typedef enum {
 
 typedef enum {
   SCSC_FP32 = 0, /* plain path: FP32 SIMT kernels on dense FP32 codes          */
-  SCSC_BF16 = 1  /* tensor path: BF16 operands on tcgen05, FP32 accumulation,
-                    FP32 master codes, FP32 residual / prox / projection        */
+  SCSC_BF16 = 1, /* tensor path: BF16 operands on tcgen05, FP32 accumulation,
+                    FP32 residual / prox / projection                          */
+  SCSC_TF32 = 2  /* TF32 operands: not built; scsc_create returns
+                    SCSC_EUNSUPPORTED (the BF16 path meets the objective bound
+                    and SCSC_FP32 is the full-precision path)                  */
 } scsc_precision;
 
 typedef enum {
@@ -75,10 +86,19 @@ typedef struct {
  * SCSC_FLAG_NO_GRAPH: tensor path launches every iteration directly instead
  *   of replaying a captured CUDA graph of the iteration loop.
  * SCSC_FLAG_NO_AUTOTUNE: tensor path skips the variant timing on the first
- *   call for a shape and uses the pipelined kernels when they apply. */
+ *   call for a shape and uses the pipelined kernels when they apply.
+ * SCSC_FLAG_UNSAMPLED_KEEP: the other reading of Sec. 3.1 (each iteration
+ *   updates the pDK sampled variables "while the rest remain unchanged"):
+ *   scsc_code_step, scsc_code_step_host and scsc_code_step_observed leave the
+ *   codes off the sampled set as they were instead of zeroing them (Eq. 4),
+ *   and the sampled codes take their proximal-gradient steps on
+ *   1/2 || x - D z ||^2 + lambda || z_S ||_1 with those codes held fixed:
+ *   x' = x - D z_off is formed once per call (FP32), then the same hot loop
+ *   runs on x'.  The ADMM and screened steps return SCSC_EUNSUPPORTED. */
 #define SCSC_FLAG_PER_IMAGE 1u
 #define SCSC_FLAG_NO_GRAPH 2u
 #define SCSC_FLAG_NO_AUTOTUNE 4u
+#define SCSC_FLAG_UNSAMPLED_KEEP 8u
 
 typedef struct {   /* host arrays, n_images entries each */
   int n_images;
@@ -242,7 +262,8 @@ scsc_status scsc_synth_backward(scsc_ctx *ctx, const scsc_batch *batch, const fl
 /* Wait for all work queued on the context, then report a device-side error
  * recorded by the tensor-core kernels: SCSC_ETIMEOUT when one of their
  * bounded waits on an mbarrier ran out (the kernel then skipped its
- * remaining work and released its tensor memory). */
+ * remaining work and released its tensor memory); else SCSC_ENONFINITE when
+ * an input check found a NaN or an infinity since the last report. */
 scsc_status scsc_sync(scsc_ctx *ctx);
 
 /* Objective of Eq. 1 for n_images images that all have H x W pixels (packed

@@ -24,6 +24,15 @@ extern "C" {
 
 scsc_status scsc_diag_tc_gemm(int N, const float *A_dev, const float *B_dev, float *D_dev);
 
+/* scsc_diag_tc_gemm_mn: the same product with B held MN-major in shared
+ * memory (the N index contiguous inside each core matrix), the layout in
+ * which the synthesis reads the adjoint's filter image.  swap = 0 puts the
+ * K-direction core stride in the descriptor's leading-dimension offset field
+ * and the N-direction stride in the stride-dimension field; swap = 1 the
+ * other way round.  Returns as scsc_diag_tc_gemm. */
+scsc_status scsc_diag_tc_gemm_mn(int N, const float *A_dev, const float *B_dev, float *D_dev,
+                                 int swap);
+
 /* scsc_diag_wait_timeout launches one block whose thread waits on a
  * shared-memory mbarrier that nothing arrives on, through the bounded wait
  * every tensor kernel uses, with a limit of limit_ms milliseconds (0 <

@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
                 "orc_project_filters": (None, [i, i, P]),
                 "orc_objective_image": (dbl, [i, i, i, i, P, P, P, dbl]),
                 "orc_code_update_image": (None, [i, i, i, i, P, P, P, P, dbl, dbl, i]),
+                "orc_code_update_image_keep": (None, [i, i, i, i, P, P, P, P, dbl, dbl, i]),
                 "orc_objective_image_observed": (dbl, [i, i, i, i, P, P, P, P, dbl]),
                 "orc_code_update_image_observed": (None, [i, i, i, i, P, P, P, P, P, dbl, dbl,
                                                           i]),

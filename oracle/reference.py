@@ -167,10 +167,12 @@ def lipschitz_filters(cfg: Config, batch: Batch, z) -> float:
 
 
 def code_step(cfg: Config, batch: Batch, x, d, z, t: int, n_iters: int,
-              step: float | None = None) -> np.ndarray:
+              step: float | None = None, keep: bool = False) -> np.ndarray:
     """One outer iteration of the code update (Alg. 1 lines 4-7 / Alg. 2
     lines 5-7): draw M^t, solve Eq. 3 by n_iters proximal-gradient steps from
-    the warm start, return the Eq. 4 codes.  ``step`` overrides 1/L_z."""
+    the warm start, return the Eq. 4 codes.  ``step`` overrides 1/L_z.
+    ``keep``: the variant where codes off the sampled set keep their values
+    (Sec. 3.1, the rest remain unchanged) instead of Eq. 4's zeros."""
     x, d = _f64(x), _f64(d)
     z = _f64(z).copy()
     if step is None:
@@ -183,8 +185,8 @@ def code_step(cfg: Config, batch: Batch, x, d, z, t: int, n_iters: int,
         m = mask_image(cfg, t, int(batch.ids[n]), H, W).ravel()
         zi = np.ascontiguousarray(batch.image(z, n, cfg.K))
         xi = np.ascontiguousarray(batch.image(x, n))
-        lib().orc_code_update_image(cfg.K, cfg.s, H, W, _p(d), _p(xi), _p(zi), _p(m),
-                                    alpha, cfg.lam, n_iters)
+        update = lib().orc_code_update_image_keep if keep else lib().orc_code_update_image
+        update(cfg.K, cfg.s, H, W, _p(d), _p(xi), _p(zi), _p(m), alpha, cfg.lam, n_iters)
         o = int(batch.off[n]) * cfg.K
         z[o:o + zi.size] = zi
     return z

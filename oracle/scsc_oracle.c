@@ -176,6 +176,29 @@ void orc_code_update_image(int K, int s, int H, int W, const double *d,
   free(g);
 }
 
+/* Variant of the code update for the other reading of Sec. 3.1 (each
+ * iteration works on the pDK sampled variables while the rest remain
+ * unchanged): codes off the sampled set keep their previous values instead of
+ * Eq. 4's zeros, and the sampled ones take n_iters proximal-gradient steps on
+ * 1/2 || x - D z ||^2 + lambda || z_S ||_1 with z off S held fixed, i.e. with
+ * the residual of all the codes. */
+void orc_code_update_image_keep(int K, int s, int H, int W, const double *d,
+                                const double *x, double *z, const uint8_t *mask,
+                                double alpha, double lambda, int n_iters) {
+  size_t D = (size_t)H * W, DK = D * (size_t)K;
+  double *r = (double *)malloc(D * sizeof(double));
+  double *g = (double *)malloc(DK * sizeof(double));
+  for (int it = 0; it < n_iters; ++it) {
+    orc_synthesis(K, s, H, W, d, z, r);
+    for (size_t i = 0; i < D; ++i) r[i] -= x[i];
+    orc_adjoint(K, s, H, W, d, r, g);
+    for (size_t i = 0; i < DK; ++i)
+      if (mask[i]) z[i] = orc_soft_threshold(z[i] - alpha * g[i], alpha * lambda);
+  }
+  free(r);
+  free(g);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Inpainting: observed pixels only in the data term (Sec. 4.3)              */
 /* ------------------------------------------------------------------------ */

@@ -69,6 +69,11 @@ double orc_objective_image(int K, int s, int H, int W, const double *d,
 void orc_code_update_image(int K, int s, int H, int W, const double *d,
                            const double *x, double *z, const uint8_t *mask,
                            double alpha, double lambda, int n_iters);
+/* orc_code_update_image with the codes off the sampled set kept (not zeroed):
+ * the sampled codes are updated against the residual of all the codes. */
+void orc_code_update_image_keep(int K, int s, int H, int W, const double *d,
+                                const double *x, double *z, const uint8_t *mask,
+                                double alpha, double lambda, int n_iters);
 
 /* Inpainting (Sec. 4.3, reconstruction from partially observed pixels): the
  * data term only counts observed pixels, 0.5 || O (x - D z) ||^2 with

@@ -492,13 +492,54 @@ __global__ void project_step_kernel(float *d, const float *G, const double *Gd, 
   }
 }
 
-__global__ void check_finite_kernel(const float *a, int64_t n, int *flag) {
+// *flag = 1 if any of a[0, n) is NaN or +-Inf.  The aligned body is read as
+// float4 (coalesced 16-byte loads), the unaligned head and the tail as floats;
+// the bits are tested (exponent all ones) so that fast-math cannot drop it.
+__device__ __forceinline__ bool nonfinite_bits(float v) {
+  return (__float_as_uint(v) & 0x7F800000u) == 0x7F800000u;
+}
+__global__ void check_finite_kernel(const float *a, int64_t head, int64_t n4, int64_t n,
+                                    int *flag) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  bool bad = false;
+  const float4 *a4 = reinterpret_cast<const float4 *>(a + head);
+  for (int64_t i = tid; i < n4; i += stride) {
+    const float4 v = a4[i];
+    bad |= nonfinite_bits(v.x) | nonfinite_bits(v.y) | nonfinite_bits(v.z) | nonfinite_bits(v.w);
+  }
+  for (int64_t i = tid; i < head; i += stride) bad |= nonfinite_bits(a[i]);
+  for (int64_t i = head + 4 * n4 + tid; i < n; i += stride) bad |= nonfinite_bits(a[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+// bits_out = the complement of bits_in on the K filters of every pixel
+// (unused high bits of each pixel's last word stay zero).
+__global__ void complement_bits_kernel(const uint32_t *in, uint32_t *out, int64_t n_words, int KW,
+                                       int K) {
+  const uint32_t last = (K & 31) ? ((1u << (K & 31)) - 1u) : 0xFFFFFFFFu;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_words;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int w = (int)(i % KW);
+    out[i] = ~in[i] & (w == KW - 1 ? last : 0xFFFFFFFFu);
+  }
+}
+
+__global__ void negate_kernel(float *a, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    if (!isfinite(a[i])) {
-      *flag = 1;
-      return;
-    }
+    a[i] = -a[i];
+}
+
+// z <- zs on the sampled set, z unchanged elsewhere.
+__global__ void merge_sampled_kernel(int64_t total, int K, int KW, const uint32_t *bits,
+                                     const float *zs, float *z) {
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pix = g / K;
+    const int k = (int)(g - pix * K);
+    if (bit_of(bits, pix, KW, k)) z[g] = zs[g];
+  }
 }
 
 template <typename F>
@@ -644,8 +685,37 @@ cudaError_t launch_project_step(float *d, const float *G, const double *Gd, cons
 }
 
 cudaError_t launch_check_finite(const float *a, int64_t n, int *flag, cudaStream_t st) {
+  if (n == 0 || a == nullptr) return cudaSuccess;
+  int64_t head = (int64_t)(((16u - ((uintptr_t)a & 15u)) & 15u) / 4u);
+  if ((uintptr_t)a & 3u) head = n;  // not even float-aligned: scalar loads only
+  if (head > n) head = n;
+  const int64_t n4 = (n - head) / 4;
+  check_finite_kernel<<<grid_for(n4 > 0 ? n4 : n, 256, 152 * 16), 256, 0, st>>>(a, head, n4, n,
+                                                                                   flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_complement_bits(const uint32_t *in, uint32_t *out, int64_t n_px, int K,
+                                   cudaStream_t st) {
+  const int KW = (K + 31) / 32;
+  const int64_t n = n_px * KW;
   if (n == 0) return cudaSuccess;
-  check_finite_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(a, n, flag);
+  complement_bits_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(in, out, n, KW, K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_negate(float *a, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  negate_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(a, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_sampled(const BatchDev &b, int K, const uint32_t *bits, const float *zs,
+                                 float *z, cudaStream_t st) {
+  const int64_t n = b.total_px * K;
+  if (n == 0) return cudaSuccess;
+  merge_sampled_kernel<<<grid_for(n, 256, 152 * 64), 256, 0, st>>>(n, K, (K + 31) / 32, bits, zs,
+                                                                    z);
   return cudaGetLastError();
 }
 

@@ -131,8 +131,11 @@ __global__ void scan_add_kernel(uint64_t *out, int n, const uint64_t *block_sums
   if (i < n) out[i] += block_sums[blockIdx.x];
 }
 
-// mode 0: packed <- z on the sampled set (warm start)
+// mode 0: packed <- z on the sampled set (warm start); *nonfinite |= 1 if
+//         any code of the item is NaN or infinite
 // mode 1: z <- packed on the sampled set, 0 elsewhere (Eq. 4)
+// mode 2: z <- packed on the sampled set, unchanged elsewhere (the variant
+//         that keeps the unsampled codes)
 // One block per item.  The item's dense codes are one contiguous block of
 // npx * K floats, walked linearly by the block (coalesced); each element
 // finds its packed slot from per-pixel chunk offsets staged in shared memory.
@@ -141,7 +144,7 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int K
                                                         const uint32_t *bits,
                                                         const uint64_t *seg_base,
                                                         const uint16_t *pxoff, float *packed,
-                                                        float *z, int mode) {
+                                                        float *z, int mode, int *nonfinite) {
   __shared__ uint16_t s_m[kMaxChunks][kStrip];
   __shared__ uint32_t s_off[kMaxChunks][kStrip];
   const int q = blockIdx.x;
@@ -165,6 +168,7 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int K
   constexpr int kU = 4;
   int pl = threadIdx.x / K, k = threadIdx.x - pl * K;
   const int dpl = kThreads / K, dk = kThreads - dpl * K;
+  bool bad = false;
   for (int j0 = threadIdx.x; j0 < n; j0 += kU * kThreads) {
     float v[kU];
     uint64_t idx[kU];
@@ -195,12 +199,14 @@ __global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int K
       const int j = j0 + u * kThreads;
       if (j >= n) break;
       if (mode == 0) {
+        bad |= (__float_as_uint(v[u]) & 0x7F800000u) == 0x7F800000u;
         if (on[u]) packed[idx[u]] = v[u];
-      } else {
-        zb[j] = v[u];  // 0 off the sampled set (Eq. 4)
+      } else if (mode == 1 || on[u]) {
+        zb[j] = v[u];  // mode 1: 0 off the sampled set (Eq. 4)
       }
     }
   }
+  if (mode == 0 && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(nonfinite, 1);
 }
 
 // Dense BF16 code tile of every row item in the synthesis A-operand layout
@@ -666,6 +672,80 @@ __global__ void __launch_bounds__(kThreads) selftest_gemm_kernel(int N, const fl
   }
 }
 
+// D[128 x N] = A[128 x 64] B[N x 64]^T with B stored MN-major: core matrix
+// (n block nb, k block kb) at nb * 1024 + kb * 128 bytes, its row r holding
+// B[8 nb .. 8 nb + 7][8 kb + r] (8 N values, 16 bytes).  `swap` selects which
+// descriptor field carries the K-direction core stride (128 bytes): 0 = the
+// leading-dimension offset, 1 = the stride-dimension offset.  Either way
+// every address the MMA forms lies inside the 32 KB B buffer.
+__global__ void __launch_bounds__(kThreads) selftest_gemm_mn_kernel(int N, const float *A,
+                                                                    const float *B, float *D,
+                                                                    int swap, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint8_t *As = smem;               // 128 x 64 bf16 = 16 KB, K-major
+  uint8_t *Bs = smem + 128 * 64 * 2;  // 32 KB, MN-major
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 256);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::fence_mbar_init();
+  }
+  for (int t = tid; t < 128 * 64; t += kThreads) {
+    int row = t / 64, k = t % 64;
+    size_t o = (size_t)(k / 8) * (128 * 16) + (row / 8) * 128 + (row % 8) * 16 + (k % 8) * 2;
+    *reinterpret_cast<__nv_bfloat16 *>(As + o) = __float2bfloat16_rn(A[t]);
+  }
+  for (int t = tid; t < 32 * 1024 / 2; t += kThreads)
+    reinterpret_cast<__nv_bfloat16 *>(Bs)[t] = __float2bfloat16_rn(0.0f);
+  __syncthreads();
+  for (int t = tid; t < N * 64; t += kThreads) {
+    int n = t / 64, k = t % 64;
+    size_t o = (size_t)(n / 8) * 1024 + (k / 8) * 128 + (k % 8) * 16 + (n % 8) * 2;
+    *reinterpret_cast<__nv_bfloat16 *>(Bs + o) = __float2bfloat16_rn(B[t]);
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base;
+  if (tid == 0) {
+    const uint32_t idesc = tc::idesc_bf16_f32_bmn(128, N);
+    const uint32_t lbo = swap ? 1024 : 128, sbo = swap ? 128 : 1024;
+    for (int kk = 0; kk < 4; ++kk) {
+      uint64_t ad = tc::smem_desc(tc::smem_u32(As) + kk * 2 * 128 * 16, 128 * 16, 128);
+      uint64_t bd = tc::smem_desc(tc::smem_u32(Bs) + kk * 2 * 128, lbo, sbo);
+      tc::mma_bf16(taddr, ad, bd, idesc, kk > 0 ? 1u : 0u);
+    }
+    tc::mma_commit(&mbar);
+  }
+  bool ok = tc::mbar_wait_bounded(&mbar, 0, kWaitNs);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicExch(err, 1);
+    tc::mbar_wait_bounded(&mbar, 0, kWaitNs);
+  } else {
+    tc::fence_after_sync();
+    const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16);
+    for (int c = 0; c < N; c += 16) {
+      float v[16];
+      tc::tmem_ld16(lane_addr + c, v);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) D[(size_t)tid * N + c + e] = v[e];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, 256);
+  }
+}
+
 // ------------------------------------------------------------------ host helpers
 
 template <typename F>
@@ -740,7 +820,7 @@ void tc_release(TcWorkspace &ws) {
 cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, const int *W_host,
                          int K, int s, const float *x, const float *d, float *z,
                          const uint32_t *bits, const uint8_t *obs, const StepParams *prm,
-                         int n_iters, cudaStream_t st) {
+                         int n_iters, bool keep_unsampled, int *nonfinite, cudaStream_t st) {
   if (K > 256) {
     ws.last_error = "the tensor path supports K <= 256";
     return cudaErrorNotSupported;
@@ -808,7 +888,7 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   TRY(cudaGetLastError());
   int pr = ws.prof ? ws.prof->begin(KID_PACK, st) : -1;
   pack_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, pxoff, as<float>(ws.packed),
-                                      z, 0);
+                                      z, 0, nonfinite);
   TRY(cudaGetLastError());
   if (ws.prof) ws.prof->end(pr, st);
 
@@ -1008,7 +1088,7 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   // Eq. 4: dense codes, zero off the sampled set
   int pu = ws.prof ? ws.prof->begin(KID_UNPACK, st) : -1;
   pack_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, pxoff, as<float>(ws.packed),
-                                      z, 1);
+                                      z, keep_unsampled ? 2 : 1, nonfinite);
   TRY(cudaGetLastError());
   if (ws.prof) ws.prof->end(pu, st);
   return cudaSuccess;
@@ -1030,6 +1110,16 @@ __global__ void selftest_wait_kernel(uint64_t limit_ns, int *err) {
 
 cudaError_t tc_selftest_wait(uint64_t limit_ns, int *err, cudaStream_t st) {
   selftest_wait_kernel<<<1, 32, 0, st>>>(limit_ns, err);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_selftest_gemm_mn(int N, const float *A, const float *B, float *D, int swap,
+                                int *err, cudaStream_t st) {
+  if (N < 16 || N > 256 || N % 16 != 0) return cudaErrorInvalidValue;
+  size_t smem = 1024 + 128 * 64 * 2 + 32 * 1024;
+  TRY(cudaFuncSetAttribute(selftest_gemm_mn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem));
+  selftest_gemm_mn_kernel<<<1, kThreads, smem, st>>>(N, A, B, D, swap, err);
   return cudaGetLastError();
 }
 

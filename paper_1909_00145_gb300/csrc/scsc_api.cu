@@ -76,6 +76,7 @@ struct scsc_ctx {
   BatchCache batch, domain;     // the call's batch; the step-size domain
   int domainH = -1, domainW = -1;
   DevBuf bits, r, pix2, prm, scal, partials, gpart, gsum, pu, pw, flag;
+  DevBuf xkeep, zkeep, bits_off;  // unsampled-keep variant: x - D z_off, sampled codes, complement
   DevBuf ddtG, ddtA;  // tap Gram matrix and per-class stencils of D D^T
   DevBuf admm;        // ADMM vectors: y, u, b, A^T x, CG residual, direction, QP image
   DevBuf admm_partials;  // per-image FP64 partials of the CG dot products
@@ -232,6 +233,37 @@ int M_of(const scsc_ctx *ctx) { return ctx->cfg.s * ctx->cfg.s; }
 
 uint64_t threshold_T(const scsc_config &c) {
   return ((uint64_t)c.p_num << 32) / (uint64_t)c.p_den;
+}
+
+// Device word that the input checks set when a NaN or an infinity is found
+// (zeroed when allocated and whenever it is reported).
+int *nonfinite_word(scsc_ctx *ctx) {
+  if (!ctx->flag.p) {
+    if (ctx->flag.ensure(sizeof(int)) != cudaSuccess) return nullptr;
+    if (cudaMemsetAsync(ctx->flag.p, 0, sizeof(int), ctx->stream) != cudaSuccess) return nullptr;
+  }
+  return ctx->flag.as<int>();
+}
+
+// Enqueue the NaN / Inf check of n floats (a NULL pointer is skipped).
+scsc_status check_finite(scsc_ctx *ctx, const float *a, int64_t n) {
+  int *w = nonfinite_word(ctx);
+  if (!w) return fail(ctx, SCSC_ENOMEM, "input check: flag allocation failed");
+  CK(launch_check_finite(a, n, w, ctx->stream));
+  return SCSC_OK;
+}
+
+// After the stream has been synchronised: SCSC_ENONFINITE (and the word
+// cleared) if an input check has fired since the last report.
+scsc_status report_nonfinite(scsc_ctx *ctx) {
+  if (!ctx->flag.p) return SCSC_OK;
+  int word = 0;
+  CK(cudaMemcpy(&word, ctx->flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (word == 0) return SCSC_OK;
+  CK(cudaMemset(ctx->flag.p, 0, sizeof(int)));
+  return fail(ctx, SCSC_ENONFINITE,
+              "an input (image, codes or filters) held a NaN or an infinity; the results of the "
+              "calls since the last report are undefined");
 }
 
 scsc_status build_mask(scsc_ctx *ctx, uint64_t t) {
@@ -398,9 +430,14 @@ scsc_status check_cfg(scsc_ctx *ctx, const scsc_config *c) {
     return fail(ctx, SCSC_EINVAL, "p = %u/%u must satisfy 0 <= p <= 1", c->p_num, c->p_den);
   if (!(c->step >= 0.0) || !std::isfinite(c->step))
     return fail(ctx, SCSC_EINVAL, "step must be finite and >= 0");
+  if (c->prec == SCSC_TF32)
+    return fail(ctx, SCSC_EUNSUPPORTED,
+                "TF32 operands are not built: the tensor path uses BF16 operands (kind::f16), "
+                "and SCSC_FP32 is the full-precision path");
   if (c->prec != SCSC_FP32 && c->prec != SCSC_BF16)
     return fail(ctx, SCSC_EINVAL, "unknown precision %d", (int)c->prec);
-  if (c->flags & ~(SCSC_FLAG_PER_IMAGE | SCSC_FLAG_NO_GRAPH | SCSC_FLAG_NO_AUTOTUNE))
+  if (c->flags & ~(SCSC_FLAG_PER_IMAGE | SCSC_FLAG_NO_GRAPH | SCSC_FLAG_NO_AUTOTUNE |
+                   SCSC_FLAG_UNSAMPLED_KEEP))
     return fail(ctx, SCSC_EINVAL, "unknown flags 0x%x", c->flags);
   return SCSC_OK;
 }
@@ -438,6 +475,7 @@ scsc_status scsc_destroy(scsc_ctx *ctx) {
   for (DevBuf *b : {&ctx->bits, &ctx->r, &ctx->pix2, &ctx->prm, &ctx->scal, &ctx->partials,
                     &ctx->gpart, &ctx->gsum, &ctx->pu, &ctx->pw,
                     &ctx->flag, &ctx->ddtG, &ctx->ddtA, &ctx->admm, &ctx->admm_partials,
+                    &ctx->xkeep, &ctx->zkeep, &ctx->bits_off,
                     &ctx->hd, &ctx->hx[0], &ctx->hx[1], &ctx->hz[0], &ctx->hz[1],
                     &ctx->C, &ctx->B, &ctx->Cd, &ctx->batch.dev, &ctx->domain.dev,
                     &ctx->sg, &ctx->spref, &ctx->snrm, &ctx->spart, &ctx->simg, &ctx->skept})
@@ -475,6 +513,7 @@ scsc_status scsc_lipschitz_codes(scsc_ctx *ctx, const scsc_batch *batch, const f
   if (!ctx) return SCSC_EINVAL;
   if (!d_dev || !out_host) return fail(ctx, SCSC_EINVAL, "NULL pointer");
   CKS(stage_batch(ctx, batch));
+  CKS(check_finite(ctx, d_dev, (int64_t)ctx->cfg.K * M_of(ctx)));
   scsc_config saved = ctx->cfg;
   ctx->cfg.step = 0.0;  // always run the power iteration here
   scsc_status s = code_step_size(ctx, d_dev);
@@ -482,7 +521,7 @@ scsc_status scsc_lipschitz_codes(scsc_ctx *ctx, const scsc_batch *batch, const f
   if (s != SCSC_OK) return s;
   CK(cudaMemcpyAsync(out_host, ctx->scal.as<double>(), 8, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  return SCSC_OK;
+  return report_nonfinite(ctx);
 }
 
 // scsc_code_step / scsc_code_step_observed (obs = NULL: every pixel observed).
@@ -499,15 +538,34 @@ static scsc_status code_step_impl(scsc_ctx *ctx, const scsc_batch *batch, const 
   const BatchDev &b = ctx->batch.view;
   const int K = ctx->cfg.K, s = ctx->cfg.s;
   cudaStream_t st = ctx->stream;
+  const bool keep = (ctx->cfg.flags & SCSC_FLAG_UNSAMPLED_KEEP) != 0;
+  if (keep && keep_mask)
+    return fail(ctx, SCSC_EUNSUPPORTED, "the unsampled-keep variant has no screened step");
+  CKS(check_finite(ctx, x_dev, b.total_px));
+  CKS(check_finite(ctx, d_dev, (int64_t)K * M_of(ctx)));
   if (!keep_mask) CKS(build_mask(ctx, t));
   if (!keep_step) CKS(code_step_size(ctx, d_dev));
   const StepParams *prm = ctx->prm.as<StepParams>();
+  const uint32_t *bits = ctx->bits.as<uint32_t>();
+  if (keep) {
+    // Sec. 3.1's other reading: the codes off the sampled set stay as they
+    // are, so the sampled problem sees x' = x - D z_off (FP32, once per step)
+    CK(ctx->xkeep.ensure((size_t)b.total_px * 4));
+    CK(ctx->bits_off.ensure((size_t)b.total_px * KW_of(ctx) * 4));
+    CK(launch_complement_bits(bits, ctx->bits_off.as<uint32_t>(), b.total_px, K, st));
+    CK(launch_synth_fp32(b, K, s, d_dev, z_dev, ctx->bits_off.as<uint32_t>(), x_dev,
+                         ctx->xkeep.as<float>(), st));
+    CK(launch_negate(ctx->xkeep.as<float>(), b.total_px, st));
+    x_dev = ctx->xkeep.as<float>();
+  }
   if (ctx->cfg.prec == SCSC_BF16) {
     int *errw = tc_error_word(ctx->tc);
     if (!errw) return fail(ctx, SCSC_ENOMEM, "tensor path: error word allocation failed");
+    int *nf = nonfinite_word(ctx);
+    if (!nf) return fail(ctx, SCSC_ENOMEM, "input check: flag allocation failed");
     CK(cudaMemsetAsync(errw, 0, sizeof(int), st));
     cudaError_t e = tc_code_step(ctx->tc, b, batch->H, batch->W, K, s, x_dev, d_dev, z_dev,
-                                 ctx->bits.as<uint32_t>(), obs, prm, n_iters, st);
+                                 bits, obs, prm, n_iters, keep, nf, st);
     if (e == cudaErrorNotSupported)
       return fail(ctx, SCSC_EUNSUPPORTED, "tensor path: %s", tc_last_error(ctx->tc));
     if (e == cudaErrorTimeout)
@@ -516,7 +574,16 @@ static scsc_status code_step_impl(scsc_ctx *ctx, const scsc_batch *batch, const 
     CK(e);
     return SCSC_OK;
   }
-  // Plain FP32 path.  Eq. 4 warm start: unsampled codes are zero.
+  // Plain FP32 path.  Eq. 4 warm start: unsampled codes are zero (the keep
+  // variant iterates on a copy holding the sampled codes, merged back below).
+  CKS(check_finite(ctx, z_dev, b.total_px * K));
+  float *const z_user = z_dev;
+  if (keep) {
+    CK(ctx->zkeep.ensure((size_t)b.total_px * K * 4));
+    CK(cudaMemcpyAsync(ctx->zkeep.p, z_dev, (size_t)b.total_px * K * 4, cudaMemcpyDeviceToDevice,
+                       st));
+    z_dev = ctx->zkeep.as<float>();
+  }
   CK(launch_apply_mask_dense(b, K, ctx->bits.as<uint32_t>(), z_dev, st));
   CK(ctx->r.ensure((size_t)b.total_px * 4));
   // views to launch over: the whole batch, or each image on its own
@@ -540,6 +607,7 @@ static scsc_status code_step_impl(scsc_ctx *ctx, const scsc_batch *batch, const 
       ctx->prof.end(p2, st);
     }
   }
+  if (keep) CK(launch_merge_sampled(b, K, ctx->bits.as<uint32_t>(), z_dev, z_user, st));
   return SCSC_OK;
 }
 
@@ -551,6 +619,9 @@ static scsc_status objective_impl(scsc_ctx *ctx, const scsc_batch *batch, const 
   CKS(stage_batch(ctx, batch));
   const BatchDev &b = ctx->batch.view;
   cudaStream_t st = ctx->stream;
+  CKS(check_finite(ctx, x_dev, b.total_px));
+  CKS(check_finite(ctx, z_dev, b.total_px * ctx->cfg.K));
+  CKS(check_finite(ctx, d_dev, (int64_t)ctx->cfg.K * M_of(ctx)));
   CK(ctx->r.ensure((size_t)b.total_px * 4));
   CK(ctx->partials.ensure((size_t)2 * kRedBlocks * 8));
   CK(ctx->scal.ensure(8 * 8));
@@ -563,7 +634,7 @@ static scsc_status objective_impl(scsc_ctx *ctx, const scsc_batch *batch, const 
                        ctx->scal.as<double>() + 4, st));
   CK(cudaMemcpyAsync(out_host, ctx->scal.as<double>() + 4, 8, cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  return SCSC_OK;
+  return report_nonfinite(ctx);
 }
 
 scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
@@ -650,7 +721,8 @@ scsc_status scsc_code_step_host(scsc_ctx *ctx, const scsc_batch *batch, const fl
   }
   CK(cudaStreamSynchronize(ctx->s_out));
   CK(cudaStreamSynchronize(st));
-  return status;
+  if (status != SCSC_OK) return status;
+  return report_nonfinite(ctx);
 }
 
 scsc_status scsc_code_step_observed(scsc_ctx *ctx, const scsc_batch *batch, const float *x_dev,
@@ -676,7 +748,12 @@ scsc_status scsc_code_step_admm(scsc_ctx *ctx, const scsc_batch *batch, const fl
   if (!std::isfinite(rho) || !std::isfinite(alpha_r) || alpha_r >= 2.0)
     return fail(ctx, SCSC_EINVAL, "rho = %g, alpha = %g outside rho > 0, 0 < alpha < 2", rho,
                 alpha_r);
+  if (ctx->cfg.flags & SCSC_FLAG_UNSAMPLED_KEEP)
+    return fail(ctx, SCSC_EUNSUPPORTED, "the unsampled-keep variant has no ADMM step");
   CKS(stage_batch(ctx, batch));
+  CKS(check_finite(ctx, x_dev, ctx->batch.view.total_px));
+  CKS(check_finite(ctx, z_dev, ctx->batch.view.total_px * ctx->cfg.K));
+  CKS(check_finite(ctx, d_dev, (int64_t)ctx->cfg.K * M_of(ctx)));
   if (ctx->batch.view.n > kMaxGridImages)
     return fail(ctx, SCSC_EINVAL, "ADMM: at most %d images per call", kMaxGridImages);
   CKS(build_mask(ctx, t));
@@ -804,6 +881,8 @@ scsc_status scsc_code_step_screened(scsc_ctx *ctx, const scsc_batch *batch, cons
   if (!x_dev || !d_dev || !z_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
   if (n_iters < 0) return fail(ctx, SCSC_EINVAL, "n_iters = %d < 0", n_iters);
   if (screen_every < 1) return fail(ctx, SCSC_EINVAL, "screen_every = %d < 1", screen_every);
+  if (ctx->cfg.flags & SCSC_FLAG_UNSAMPLED_KEEP)
+    return fail(ctx, SCSC_EUNSUPPORTED, "the unsampled-keep variant has no screened step");
   CKS(stage_batch(ctx, batch));
   if (ctx->batch.view.n > kMaxGridImages)
     return fail(ctx, SCSC_EINVAL, "screening: at most %d images per call", kMaxGridImages);
@@ -838,6 +917,8 @@ scsc_status scsc_synth(scsc_ctx *ctx, const scsc_batch *batch, const float *z_de
   if (!ctx) return SCSC_EINVAL;
   if (!z_dev || !d_dev || !xhat_dev) return fail(ctx, SCSC_EINVAL, "NULL device pointer");
   CKS(stage_batch(ctx, batch));
+  CKS(check_finite(ctx, z_dev, ctx->batch.view.total_px * ctx->cfg.K));
+  CKS(check_finite(ctx, d_dev, (int64_t)ctx->cfg.K * M_of(ctx)));
   const uint32_t *bits = nullptr;
   if (masked) {
     CKS(build_mask(ctx, t));
@@ -855,6 +936,9 @@ scsc_status scsc_synth_backward(scsc_ctx *ctx, const scsc_batch *batch, const fl
   if (!grad_dev || !d_dev || (grad_d_dev && !z_dev))
     return fail(ctx, SCSC_EINVAL, "NULL device pointer");
   CKS(stage_batch(ctx, batch));
+  CKS(check_finite(ctx, grad_dev, ctx->batch.view.total_px));
+  if (grad_d_dev) CKS(check_finite(ctx, z_dev, ctx->batch.view.total_px * ctx->cfg.K));
+  CKS(check_finite(ctx, d_dev, (int64_t)ctx->cfg.K * M_of(ctx)));
   const uint32_t *bits = nullptr;
   if (masked) {
     CKS(build_mask(ctx, t));
@@ -881,6 +965,9 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
   CKS(stage_batch(ctx, batch));
   const BatchDev &b = ctx->batch.view;
   const int K = ctx->cfg.K, s = ctx->cfg.s, M = M_of(ctx);
+  CKS(check_finite(ctx, x_dev, b.total_px));
+  CKS(check_finite(ctx, z_dev, b.total_px * K));
+  CKS(check_finite(ctx, d_dev, (int64_t)K * M));
   cudaStream_t st = ctx->stream;
   CK(ctx->scal.ensure(8 * 8));
   if (mode == SCSC_DICT_BATCH) {
@@ -953,7 +1040,7 @@ scsc_status scsc_sync(scsc_ctx *ctx) {
     if (word != 0)
       return fail(ctx, SCSC_ETIMEOUT, "a tensor-core kernel's bounded wait ran out");
   }
-  return SCSC_OK;
+  return report_nonfinite(ctx);
 }
 
 scsc_status scsc_diag_profile(scsc_ctx *ctx, int enable) {
@@ -980,6 +1067,24 @@ scsc_status scsc_diag_tc_gemm(int N, const float *A_dev, const float *B_dev, flo
   scsc_status s = SCSC_OK;
   if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
       tc_selftest_gemm(N, A_dev, B_dev, D_dev, err, nullptr) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    s = SCSC_ECUDA;
+  } else {
+    int word = 0;
+    if (cudaMemcpy(&word, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) s = SCSC_ECUDA;
+    else if (word) s = SCSC_ETIMEOUT;
+  }
+  cudaFree(err);
+  return s;
+}
+
+scsc_status scsc_diag_tc_gemm_mn(int N, const float *A_dev, const float *B_dev, float *D_dev,
+                                 int swap) {
+  int *err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return SCSC_ENOMEM;
+  scsc_status s = SCSC_OK;
+  if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
+      tc_selftest_gemm_mn(N, A_dev, B_dev, D_dev, swap != 0, err, nullptr) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess) {
     s = SCSC_ECUDA;
   } else {

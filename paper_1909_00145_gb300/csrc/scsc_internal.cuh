@@ -142,7 +142,15 @@ cudaError_t launch_power_finish(const double *partials, int n_blocks, double saf
                                 StepParams *prm, cudaStream_t st);
 cudaError_t launch_project_step(float *d, const float *G_or_null, const double *Gd_or_null,
                                 const double *L, int K, int M, cudaStream_t st);
+// *flag |= 1 when a[0, n) holds a NaN or an infinity.
 cudaError_t launch_check_finite(const float *a, int64_t n, int *flag, cudaStream_t st);
+// out = complement of in over the K filter bits of each of n_px pixels.
+cudaError_t launch_complement_bits(const uint32_t *in, uint32_t *out, int64_t n_px, int K,
+                                   cudaStream_t st);
+cudaError_t launch_negate(float *a, int64_t n, cudaStream_t st);
+// z <- zs on the coordinates whose bit is set, z unchanged elsewhere.
+cudaError_t launch_merge_sampled(const BatchDev &b, int K, const uint32_t *bits, const float *zs,
+                                 float *z, cudaStream_t st);
 // Safe screening of the code problem (kernels_screen.cu): duality-gap sphere
 // test per image on its active set.  prepare: per-filter prefix sums of the
 // squared taps (pref, K (s+1)^2 doubles) and norms (nrm, K floats); stats:

@@ -66,11 +66,13 @@ struct TcWorkspace {
 // synthesis and adjoint, unpack to dense codes (Eq. 4).
 // H_host / W_host are the batch's host arrays (n images).
 // obs: one byte per pixel, nonzero = observed (data term on observed pixels
-// only); NULL = every pixel observed.
+// only); NULL = every pixel observed.  keep_unsampled: codes off the sampled
+// set are left as they are instead of zeroed (x must then already exclude
+// their contribution).  *nonfinite |= 1 when a warm-start code is NaN or Inf.
 cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, const int *W_host,
                          int K, int s, const float *x, const float *d, float *z,
                          const uint32_t *bits, const uint8_t *obs, const StepParams *prm,
-                         int n_iters, cudaStream_t st);
+                         int n_iters, bool keep_unsampled, int *nonfinite, cudaStream_t st);
 // Device error word of the tensor kernels (0 = ok, 1 = bounded wait ran out).
 int *tc_error_word(TcWorkspace &ws);
 void tc_release(TcWorkspace &ws);
@@ -80,6 +82,10 @@ const char *tc_last_error(const TcWorkspace &ws);
 // operands rounded from the float inputs, FP32 accumulation); device buffers.
 cudaError_t tc_selftest_gemm(int N, const float *A, const float *B, float *D, int *err,
                              cudaStream_t st);
+// The same product with B stored MN-major (swap: which descriptor field holds
+// the K-direction core stride).
+cudaError_t tc_selftest_gemm_mn(int N, const float *A, const float *B, float *D, int swap,
+                                int *err, cudaStream_t st);
 // One bounded mbarrier wait that nothing completes: sets *err after limit_ns.
 cudaError_t tc_selftest_wait(uint64_t limit_ns, int *err, cudaStream_t st);
 

@@ -40,6 +40,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
+// The same with B stored MN-major (bit 16: the N index is the contiguous one
+// inside each 8 x 16-byte core matrix, whose 8 rows are 8 K indices).
+__host__ __device__ constexpr uint32_t idesc_bf16_f32_bmn(int M, int N) {
+  return idesc_bf16_f32(M, N) | (1u << 16);
+}
 
 // ---- TMEM ----------------------------------------------------------------
 

@@ -24,9 +24,9 @@ c_int, c_double, c_u32, c_u64, c_i64, c_void_p, c_size_t = (
 SCSC_OK, SCSC_EINVAL, SCSC_ENOMEM, SCSC_ECUDA, SCSC_ETIMEOUT, SCSC_ENONFINITE, SCSC_EUNSUPPORTED = range(7)
 STATUS_NAMES = ["SCSC_OK", "SCSC_EINVAL", "SCSC_ENOMEM", "SCSC_ECUDA", "SCSC_ETIMEOUT",
                 "SCSC_ENONFINITE", "SCSC_EUNSUPPORTED"]
-SCSC_FP32, SCSC_BF16 = 0, 1
+SCSC_FP32, SCSC_BF16, SCSC_TF32 = 0, 1, 2
 SCSC_DICT_BATCH, SCSC_DICT_ONLINE, SCSC_DICT_BATCH_GS = 0, 1, 2
-SCSC_FLAG_PER_IMAGE, SCSC_FLAG_NO_GRAPH, SCSC_FLAG_NO_AUTOTUNE = 1, 2, 4
+SCSC_FLAG_PER_IMAGE, SCSC_FLAG_NO_GRAPH, SCSC_FLAG_NO_AUTOTUNE, SCSC_FLAG_UNSAMPLED_KEEP = 1, 2, 4, 8
 
 
 class scsc_config(ctypes.Structure):
@@ -85,6 +85,7 @@ _SIGNATURES = {
     "scsc_online_save": [c_void_p, c_void_p, c_size_t],
     "scsc_online_load": [c_void_p, c_void_p, c_size_t],
     "scsc_diag_tc_gemm": [c_int, c_void_p, c_void_p, c_void_p],
+    "scsc_diag_tc_gemm_mn": [c_int, c_void_p, c_void_p, c_void_p, c_int],
     "scsc_diag_wait_timeout": [c_double],
     "scsc_objective_noalloc": [ctypes.POINTER(scsc_config), c_int, c_int, c_int, c_void_p,
                                c_void_p, c_void_p, c_void_p, c_void_p],
@@ -197,7 +198,7 @@ class Context:
         self.K, self.s, self.lam = int(K), int(s), float(lam)
         self.p = (int(p[0]), int(p[1]))
         self.seed = int(seed)
-        self.prec = {"fp32": SCSC_FP32, "bf16": SCSC_BF16}[prec]
+        self.prec = {"fp32": SCSC_FP32, "bf16": SCSC_BF16, "tf32": SCSC_TF32}[prec]
         self.cfg = scsc_config(self.K, self.s, self.lam, self.p[0], self.p[1], self.seed,
                                self.prec, float(step), int(flags))
         self.stream = stream
@@ -465,6 +466,17 @@ def scsc_diag_tc_gemm(A, B):
     N = B.shape[0]
     D = torch.empty((128, N), dtype=torch.float32, device=A.device)
     _check(lib().scsc_diag_tc_gemm(N, _ptr(A), _ptr(B), _ptr(D)), None, "scsc_diag_tc_gemm")
+    return D
+
+
+def scsc_diag_tc_gemm_mn(A, B, swap: int):
+    """tcgen05 self-check with B held MN-major: D = bf16(A) bf16(B)^T when the
+    descriptor fields carry the strides the way `swap` selects."""
+    import torch
+    N = B.shape[0]
+    D = torch.empty((128, N), dtype=torch.float32, device=A.device)
+    _check(lib().scsc_diag_tc_gemm_mn(N, _ptr(A), _ptr(B), _ptr(D), int(swap)), None,
+           "scsc_diag_tc_gemm_mn")
     return D
 
 

@@ -34,6 +34,19 @@ def test_tcgen05_gemm_selfcheck(N):
     assert rel_l2(D.numpy(), ref.numpy()) < 1e-6
 
 
+@pytest.mark.parametrize("N", [16, 176, 256])
+def test_tcgen05_gemm_mn_major_b_selfcheck(N):
+    """B held MN-major (the layout in which the synthesis reads the adjoint's
+    filter image): the leading-dimension field carries the K-direction core
+    stride, as for K-major operands."""
+    g = torch.Generator().manual_seed(N + 1)
+    A = torch.randn(128, 64, generator=g)
+    B = torch.randn(N, 64, generator=g)
+    D = scsc.scsc_diag_tc_gemm_mn(A.cuda(), B.cuda(), 0).cpu()
+    ref = A.to(torch.bfloat16).double() @ B.to(torch.bfloat16).double().T
+    assert rel_l2(D.numpy(), ref.numpy()) < 1e-6
+
+
 # ------------------------------------------------------------------ mask
 
 @pytest.mark.parametrize("K,p,H,W", [(16, (1, 2), [100], [100]), (100, (1, 4), [37, 20], [50, 131]),

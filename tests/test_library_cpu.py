@@ -47,7 +47,7 @@ def test_library_is_built_for_sm103a():
 def test_config_validation_happens_on_the_host():
     L = scsc.lib()
     bad = [dict(K=0), dict(K=600), dict(s=4), dict(s=13), dict(lam=0.0), dict(p=(3, 2)),
-           dict(p=(1, 0)), dict(step=-1.0), dict(flags=8), dict(prec=2)]
+           dict(p=(1, 0)), dict(step=-1.0), dict(flags=16), dict(prec=3)]
     for kw in bad:
         args = dict(K=16, s=11, lam=1.0, p=(1, 2), step=0.0, flags=0, prec=0)
         args.update(kw)
@@ -123,3 +123,16 @@ def test_objective_noalloc_binding_checks_buffers_before_any_launch():
         with pytest.raises(ValueError):
             scsc.scsc_objective_noalloc(K, s, 1.0, n, H, W, args["x"], args["z"], args["d"],
                                         args["out"])
+
+
+def test_tf32_is_declared_and_reported_unsupported_on_the_host():
+    """SCSC_TF32 is part of the precision enum; scsc_create rejects it with
+    SCSC_EUNSUPPORTED (not EINVAL) before touching the device."""
+    L = scsc.lib()
+    cfg = scsc.scsc_config(16, 11, 1.0, 1, 2, 0, scsc.SCSC_TF32, 0.0, 0)
+    h = ctypes.c_void_p()
+    assert L.scsc_create(ctypes.byref(cfg), None, ctypes.byref(h)) == scsc.SCSC_EUNSUPPORTED
+    assert not h
+    text = open(os.path.join(ROOT, "include", "scsc.h")).read()
+    assert "SCSC_TF32 = 2" in text and "SCSC_ENONFINITE = 5" in text
+    assert "SCSC_FLAG_UNSAMPLED_KEEP 8u" in text

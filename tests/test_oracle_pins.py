@@ -235,6 +235,38 @@ def test_subsampled_pg_matches_explicit_matrix_pg():
             assert m.all()
 
 
+def test_keep_variant_matches_explicit_matrix_pg_with_fixed_unsampled_codes():
+    """Sec. 3.1's other reading: the unsampled codes remain unchanged and the
+    sampled ones take proximal-gradient steps on the full residual, written
+    here with the explicit A; p = 1 is the Eq. 4 update and p = 0 leaves the
+    codes as they are."""
+    K, s, H, W = 3, 5, 8, 9
+    d = I.filters(21, K, s).astype(np.float64)
+    x = I.images(22, [H], [W]).astype(np.float64)
+    A = explicit_synthesis_matrix(d, H, W)
+    batch = R.Batch(H=[H], W=[W], ids=[6])
+    alpha = 1.0 / (1.01 * np.linalg.eigvalsh(A @ A.T).max())
+    z0 = rng(23).normal(size=H * W * K) * 0.1
+    cfg = R.Config(K=K, s=s, lam=0.03, p_num=1, p_den=3, seed=4)
+    got = R.code_step(cfg, batch, x, d, z0, t=2, n_iters=25, step=alpha, keep=True)
+    m = R.mask_image(cfg, 2, 6, H, W).ravel().astype(bool)
+    z = z0.copy()
+    for _ in range(25):
+        v = z - alpha * (A.T @ (A @ z - x))
+        z = np.where(m, np.sign(v) * np.maximum(np.abs(v) - alpha * cfg.lam, 0.0), z)
+    np.testing.assert_allclose(got, z, rtol=0, atol=1e-12)
+    assert np.array_equal(got[~m], z0[~m]) and (~m).sum() > 0
+    # the same sampled codes as the Eq. 4 update on x' = x - D z_{not S}
+    z_off = np.where(m, 0.0, z0)
+    eq4 = R.code_step(cfg, batch, x - A @ z_off, d, z0, t=2, n_iters=25, step=alpha)
+    np.testing.assert_allclose(got[m], eq4[m], rtol=0, atol=1e-12)
+    full = R.Config(K=K, s=s, lam=0.03, p_num=1, p_den=1, seed=4)
+    assert np.array_equal(R.code_step(full, batch, x, d, z0, 2, 7, step=alpha, keep=True),
+                          R.code_step(full, batch, x, d, z0, 2, 7, step=alpha))
+    none = R.Config(K=K, s=s, lam=0.03, p_num=0, p_den=1, seed=4)
+    assert np.array_equal(R.code_step(none, batch, x, d, z0, 2, 7, step=alpha, keep=True), z0)
+
+
 # ------------------------------------------------------------------ prox / projection
 
 def test_soft_threshold_is_the_prox_of_the_l1_norm():
