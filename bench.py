@@ -503,8 +503,8 @@ def main():
         for i in range(prof_steps):
             code_step(ctx, x, d, z, 100 + i)
         ctx.sync()
-        for name in ["synth_tc", "adj_tc", "finalize_r", "synth_fp32", "adjoint_fp32", "pack",
-                     "unpack", "power", "mask", "screen"]:
+        for name in ["fused", "synth_tc", "adj_tc", "finalize_r", "synth_fp32", "adjoint_fp32",
+                     "pack", "unpack", "power", "mask", "screen"]:
             tot, n = scsc.scsc_diag_kernel_time(ctx, name)
             if n:
                 kt[name] = (tot, n)
@@ -539,9 +539,18 @@ def main():
         # one launch covers the whole batch, or one image with --per-image:
         # time the kernel per PG iteration of the batch
         per_iter = len(H) if args.per_image else 1
-        avg_s = kt[dom][0] / (kt[dom][1] / per_iter) / 1e3
+        n_launch = kt[dom][1] / per_iter
+        if dom == "fused":
+            # one synthesis-only launch per step, then one per PG iteration:
+            # its time is charged to the iterations
+            n_launch -= prof_steps
+        avg_s = kt[dom][0] / n_launch / 1e3
         # algorithmic bytes per launch (stated per kernel in the design notes)
         bytes_per_launch = {
+            # the metric's algorithmic bytes per PG iteration (per pix*filter:
+            # BF16 packed codes read and written 2 p b_z, one mask bit, the
+            # image amortised over K, i.e. 2 p 2 + 1/8 + 4/K)
+            "fused": 4 * sampled + npx * K / 8 + 4 * npx,
             # packed r+w, mask, and the residual: r itself with an observation
             # mask, else the synthesis output and the image it is formed from
             "adj_tc": 8 * sampled + 4 * kw * npx + (4 if obs is not None else 8) * npx,

@@ -55,7 +55,9 @@ typedef enum {
 typedef enum {
   SCSC_FP32 = 0, /* plain path: FP32 SIMT kernels on dense FP32 codes          */
   SCSC_BF16 = 1, /* tensor path: BF16 operands on tcgen05, FP32 accumulation,
-                    FP32 residual / prox / projection                          */
+                    FP32 residual / prox / projection; the sampled codes are
+                    stored in BF16 between iterations by the fused kernel
+                    (K <= 112 at s = 11), in FP32 by the two-kernel path       */
   SCSC_TF32 = 2  /* TF32 operands: not built; scsc_create returns
                     SCSC_EUNSUPPORTED (the BF16 path meets the objective bound
                     and SCSC_FP32 is the full-precision path)                  */
@@ -99,6 +101,10 @@ typedef struct {
 #define SCSC_FLAG_NO_GRAPH 2u
 #define SCSC_FLAG_NO_AUTOTUNE 4u
 #define SCSC_FLAG_UNSAMPLED_KEEP 8u
+/* SCSC_FLAG_TWO_KERNEL: tensor path runs its two-kernel pipeline (adjoint +
+ *   prox, then synthesis; FP32 packed codes) even where the fused
+ *   one-launch-per-iteration kernel (BF16 packed codes) applies. */
+#define SCSC_FLAG_TWO_KERNEL 16u
 
 typedef struct {   /* host arrays, n_images entries each */
   int n_images;

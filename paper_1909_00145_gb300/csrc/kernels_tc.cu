@@ -72,7 +72,8 @@ __global__ void prep_filters_kernel(const float *d, int K, int S, int Kp, __nv_b
 // exclusive offsets of its 128 pixels' values inside it.
 __global__ void __launch_bounds__(kThreads) seg_count_kernel(ItemMap im, int KW,
                                                              const uint32_t *bits,
-                                                             uint32_t *counts, uint16_t *pxoff) {
+                                                             uint32_t *counts, uint16_t *pxoff,
+                                                             int pad) {
   __shared__ int sh[4];
   const int q = blockIdx.x;
   const Item it = item_of(im, q);
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kThreads) seg_count_kernel(ItemMap im, int KW,
   int total;
   const int off = scan128(cnt, sh, total);
   pxoff[(int64_t)q * kStrip + threadIdx.x] = (uint16_t)off;
-  if (threadIdx.x == 0) counts[q] = (uint32_t)(total + ((4 - (total & 3)) & 3));
+  if (threadIdx.x == 0) counts[q] = (uint32_t)((total + pad - 1) / pad * pad);
 }
 
 // Exclusive scan u32 -> u64 in three passes over blocks of 1024 elements.
@@ -238,6 +239,97 @@ __global__ void __launch_bounds__(kThreads) abuf_kernel(ItemMap im, int Kp, int 
         make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]), pack_bf16x2(v[12], v[13]),
                    pack_bf16x2(v[14], v[15]));
   }
+}
+
+// BF16 packed codes of the fused path (a multiple of 8 values per item) and
+// the A-tile element index of each value, e = (k / 8) * 1024 + (p / 8) * 64 +
+// (p % 8) * 8 + k % 8 (0xFFFF for the padding).
+// mode 0: vals <- BF16(z) on the sampled set and idx <- e (warm start), the
+//         padding set to 0 / 0xFFFF; *nonfinite |= 1 if a code is NaN or Inf
+// mode 1: z <- vals on the sampled set, 0 elsewhere (Eq. 4)
+// mode 2: z <- vals on the sampled set, unchanged elsewhere
+// One block per item, as pack_kernel.
+__global__ void __launch_bounds__(kThreads) pack16_kernel(ItemMap im, int K, int KW, int NC,
+                                                          const uint32_t *bits,
+                                                          const uint64_t *seg_base,
+                                                          const uint16_t *pxoff, uint16_t *vals,
+                                                          uint16_t *idx, float *z, int mode,
+                                                          int *nonfinite) {
+  __shared__ uint16_t s_m[kMaxChunks][kStrip];
+  __shared__ uint32_t s_off[kMaxChunks][kStrip];
+  __shared__ uint32_t s_total;
+  const int q = blockIdx.x;
+  const Item it = item_of(im, q);
+  const int col = it.js * kStrip + threadIdx.x;
+  const uint64_t item_base = seg_base[q];
+  uint32_t run = pxoff[(int64_t)q * kStrip + threadIdx.x];
+  for (int c = 0; c < NC; ++c) {
+    const uint32_t m = chunk_mask(bits, KW, it, it.a, col, c);
+    s_m[c][threadIdx.x] = (uint16_t)m;
+    s_off[c][threadIdx.x] = run;
+    run += __popc(m);
+  }
+  if (threadIdx.x == kStrip - 1) s_total = run;
+  __syncthreads();
+  if (mode == 0) {
+    // padding up to the next multiple of 8
+    const uint64_t item_end = seg_base[q + 1];
+    for (uint64_t j = item_base + s_total + threadIdx.x; j < item_end; j += kThreads) {
+      vals[j] = 0;
+      idx[j] = 0xFFFFu;
+    }
+  }
+  const int npx = min(kStrip, it.W - it.js * kStrip);
+  float *zb = z + (it.base + (int64_t)it.a * it.W + it.js * kStrip) * K;
+  const int n = npx * K;
+  constexpr int kU = 4;
+  int pl = threadIdx.x / K, k = threadIdx.x - pl * K;
+  const int dpl = kThreads / K, dk = kThreads - dpl * K;
+  bool bad = false;
+  for (int j0 = threadIdx.x; j0 < n; j0 += kU * kThreads) {
+    float v[kU];
+    uint64_t ix[kU];
+    uint32_t e[kU];
+    bool on[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = j0 + u * kThreads;
+      on[u] = false;
+      ix[u] = 0;
+      e[u] = 0;
+      v[u] = 0.0f;
+      if (j < n) {
+        const int c = k >> 4, b = k & 15;
+        const uint32_t m = s_m[c][pl];
+        on[u] = (m >> b) & 1u;
+        ix[u] = item_base + s_off[c][pl] + __popc(m & ((1u << b) - 1u));
+        e[u] = (uint32_t)((k >> 3) * 1024 + (pl >> 3) * 64 + (pl & 7) * 8 + (k & 7));
+        if (mode == 0) v[u] = zb[j];
+        else if (on[u]) v[u] = __uint_as_float((uint32_t)vals[ix[u]] << 16);
+        pl += dpl;
+        k += dk;
+        if (k >= K) {
+          k -= K;
+          ++pl;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kU; ++u) {
+      const int j = j0 + u * kThreads;
+      if (j >= n) break;
+      if (mode == 0) {
+        bad |= (__float_as_uint(v[u]) & 0x7F800000u) == 0x7F800000u;
+        if (on[u]) {
+          vals[ix[u]] = __bfloat16_as_ushort(__float2bfloat16_rn(v[u]));
+          idx[ix[u]] = (uint16_t)e[u];
+        }
+      } else if (mode == 1 || on[u]) {
+        zb[j] = v[u];
+      }
+    }
+  }
+  if (mode == 0 && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(nonfinite, 1);
 }
 
 // ------------------------------------------------------------------ synthesis
@@ -795,6 +887,136 @@ cudaError_t launch_adj2(const tcitems::ItemMap &im, int K, int s, const uint32_t
                         int grid, cudaStream_t st);
 size_t tc_abuf_bytes(int K, int Q);
 cudaError_t prepare_pipe(int K, int s, int max_smem);
+int fused_chunk_buffers(int K, int s, int max_smem);
+cudaError_t prepare_fused(int K, int s, int ncb);
+cudaError_t launch_fused(const tcitems::ItemMap &im, int K, int s, int mode, int ncb,
+                         const uint64_t *seg_base, const uint16_t *vin, uint16_t *vout,
+                         const uint16_t *idx, const uint4 *bimg, const float *xin,
+                         const float *sin, float *xout, float *sout, const float *x,
+                         const uint8_t *obs, const StepParams *prm, int *err, int grid,
+                         cudaStream_t st);
+
+namespace {
+// Launch `n` iterations (iteration(it), it = 0..n-1) as one CUDA graph: the
+// graph captured for key gk is replayed if one of the slots holds it, else it
+// is captured into the least recently used slot.
+template <typename F>
+cudaError_t replay_graph(TcWorkspace &ws, const GraphKey &gk, int n, F &&iteration,
+                         cudaStream_t st) {
+  GraphSlot *slot = nullptr;
+  for (GraphSlot &g : ws.graphs_cached)
+    if (g.exec && std::memcmp(&gk, &g.key, sizeof gk) == 0) slot = &g;
+  if (!slot) {
+    slot = &ws.graphs_cached[0];
+    for (GraphSlot &g : ws.graphs_cached)
+      if (!g.exec || g.used < slot->used) slot = &g;
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    slot->exec = nullptr;
+    cudaGraph_t g = nullptr;
+    TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (int it = 0; it < n && err == cudaSuccess; ++it) err = iteration(it);
+    cudaError_t e2 = cudaStreamEndCapture(st, &g);
+    if (err == cudaSuccess) err = e2;
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&slot->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    TRY(err);
+    slot->key = gk;
+  }
+  slot->used = ++ws.graph_clock;
+  return cudaGraphLaunch(slot->exec, st);
+}
+
+// The fused path of tc_code_step (seg_base and pxoff already built with a
+// multiple of 8 values per item): BF16 packed warm start and A-tile indices,
+// the synthesis of the warm start, n_iters fused iterations alternating
+// between two sets of buffers (replayed from a CUDA graph), unpack.
+cudaError_t fused_code_step(TcWorkspace &ws, const ItemMap &im, int Q, const BatchDev &b, int K,
+                            int s, const float *x, float *z, const uint32_t *bits,
+                            const uint64_t *seg_base, const uint16_t *pxoff, const uint8_t *obs,
+                            const StepParams *prm, int n_iters, bool keep_unsampled,
+                            int *nonfinite, int ncb, cudaStream_t st) {
+  const int Kp = (K + 15) / 16 * 16, NC = Kp / 16, KW = (K + 31) / 32, C = (s - 1) / 2;
+  if (n_iters == 0) {
+    // no step: only Eq. 4 (or nothing, for the keep variant) on the warm
+    // start, which must not go through the BF16 packed storage
+    if (!keep_unsampled) TRY(launch_apply_mask_dense(b, K, bits, z, st));
+    return launch_check_finite(z, b.total_px * K, nonfinite, st);
+  }
+  // values: at most K per pixel plus 7 padding per item
+  const size_t nval = (size_t)b.total_px * K + 8 * (size_t)Q + 16;
+  TRY(ensure(ws.v16[0], nval * 2));
+  TRY(ensure(ws.v16[1], nval * 2));
+  TRY(ensure(ws.idx16, nval * 2));
+  TRY(ensure(ws.xcore2, (size_t)b.total_px * 4));
+  TRY(ensure(ws.spill2, (size_t)Q * (2 * C > 0 ? 2 * C : 1) * 4));
+  uint16_t *v[2] = {as<uint16_t>(ws.v16[0]), as<uint16_t>(ws.v16[1])};
+  float *xc[2] = {as<float>(ws.xcore), as<float>(ws.xcore2)};
+  float *sp[2] = {as<float>(ws.spill), as<float>(ws.spill2)};
+  uint16_t *idx = as<uint16_t>(ws.idx16);
+  int pr = ws.prof ? ws.prof->begin(KID_PACK, st) : -1;
+  pack16_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, pxoff, v[0], idx, z, 0,
+                                        nonfinite);
+  TRY(cudaGetLastError());
+  if (ws.prof) ws.prof->end(pr, st);
+  TRY(prepare_fused(K, s, ncb));
+  const int grid = std::min(Q, ws.sm_count);
+  const uint4 *bimg = as<uint4>(ws.badj);
+  int *err = as<int>(ws.err);
+  // the synthesis of the warm start: the first iteration's input
+  int p0 = ws.prof ? ws.prof->begin(KID_FUSED, st) : -1;
+  TRY(launch_fused(im, K, s, 0, ncb, seg_base, v[0], nullptr, idx, bimg, nullptr, nullptr, xc[0],
+                   sp[0], x, obs, prm, err, grid, st));
+  if (ws.prof) ws.prof->end(p0, st);
+  auto iteration = [&](int it) -> cudaError_t {
+    const int i = it & 1, o = i ^ 1;
+    int p1 = ws.prof ? ws.prof->begin(KID_FUSED, st) : -1;
+    TRY(launch_fused(im, K, s, 1, ncb, seg_base, v[i], v[o], idx, bimg, xc[i], sp[i], xc[o],
+                     sp[o], x, obs, prm, err, grid, st));
+    if (ws.prof) ws.prof->end(p1, st);
+    return cudaSuccess;
+  };
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  TRY(cudaStreamIsCapturing(st, &cap));
+  const bool use_graph = ws.graphs && n_iters > 0 && st != nullptr &&
+                         cap == cudaStreamCaptureStatusNone && !(ws.prof && ws.prof->on);
+  if (use_graph) {
+    GraphKey gk{};  // zero-filled, so that memcmp sees no padding bytes
+    gk.seg_base = seg_base;
+    gk.v16a = ws.v16[0].p;
+    gk.v16b = ws.v16[1].p;
+    gk.idx16 = idx;
+    gk.badj = ws.badj.p;
+    gk.xcore = ws.xcore.p;
+    gk.spill = ws.spill.p;
+    gk.xcore2 = ws.xcore2.p;
+    gk.spill2 = ws.spill2.p;
+    gk.err = ws.err.p;
+    gk.x = x;
+    gk.prm = prm;
+    gk.item0 = ws.item0.p;
+    gk.off = b.off;
+    gk.obs = obs;
+    gk.total_px = b.total_px;
+    gk.n_images = b.n;
+    gk.K = K;
+    gk.s = s;
+    gk.Q = Q;
+    gk.variant = 2 + 8 * ncb;
+    gk.iters = n_iters;
+    TRY(replay_graph(ws, gk, n_iters, iteration, st));
+  } else {
+    for (int it = 0; it < n_iters; ++it) TRY(iteration(it));
+  }
+  // Eq. 4 (or the keep variant): dense codes from the last iterate
+  int pu = ws.prof ? ws.prof->begin(KID_UNPACK, st) : -1;
+  pack16_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, pxoff, v[n_iters & 1],
+                                        idx, z, keep_unsampled ? 2 : 1, nonfinite);
+  TRY(cudaGetLastError());
+  if (ws.prof) ws.prof->end(pu, st);
+  return cudaSuccess;
+}
+}  // namespace
 
 int *tc_error_word(TcWorkspace &ws) {
   if (ensure(ws.err, sizeof(int)) != cudaSuccess) return nullptr;
@@ -810,7 +1032,8 @@ void tc_release(TcWorkspace &ws) {
   }
   for (TcWorkspace::Buf *b : {&ws.item0, &ws.seg_count, &ws.seg_base, &ws.pxoff, &ws.scan_blocks,
                               &ws.packed, &ws.xcore, &ws.spill, &ws.r, &ws.badj, &ws.bsyn,
-                              &ws.err, &ws.abuf}) {
+                              &ws.err, &ws.abuf, &ws.v16[0], &ws.v16[1], &ws.idx16, &ws.xcore2,
+                              &ws.spill2}) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
     b->bytes = 0;
@@ -870,13 +1093,23 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   TRY(ensure(ws.bsyn, (size_t)Kp * 16 * s * 2));
   TRY(ensure(ws.err, sizeof(int)));
 
+  if (ws.max_smem == 0) {
+    int dev;
+    TRY(cudaGetDevice(&dev));
+    TRY(cudaDeviceGetAttribute(&ws.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  }
+  // the fused kernel (BF16 packed codes) where it fits, else the two-kernel
+  // paths (FP32 packed codes)
+  const int fused_ncb = ws.fused ? fused_chunk_buffers(K, s, ws.max_smem) : 0;
+  const bool use_fused = fused_ncb > 0;
   // filter operand images, sampled-code layout, warm start
   prep_filters_kernel<<<64, 256, 0, st>>>(d, K, s, Kp, as<__nv_bfloat16>(ws.badj),
                                           as<__nv_bfloat16>(ws.bsyn));
   TRY(cudaGetLastError());
   if (Q == 0) return cudaSuccess;
   uint16_t *pxoff = as<uint16_t>(ws.pxoff);
-  seg_count_kernel<<<Q, kThreads, 0, st>>>(im, KW, bits, as<uint32_t>(ws.seg_count), pxoff);
+  seg_count_kernel<<<Q, kThreads, 0, st>>>(im, KW, bits, as<uint32_t>(ws.seg_count), pxoff,
+                                           use_fused ? 8 : 4);
   TRY(cudaGetLastError());
   uint64_t *seg_base = as<uint64_t>(ws.seg_base);
   scan_local_kernel<<<nblk, 1024, 0, st>>>(as<uint32_t>(ws.seg_count), seg_base, (int)nseg,
@@ -886,17 +1119,15 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   TRY(cudaGetLastError());
   scan_add_kernel<<<nblk, 1024, 0, st>>>(seg_base, (int)nseg, as<uint64_t>(ws.scan_blocks));
   TRY(cudaGetLastError());
+  if (use_fused)
+    return fused_code_step(ws, im, Q, b, K, s, x, z, bits, seg_base, pxoff, obs, prm, n_iters,
+                           keep_unsampled, nonfinite, fused_ncb, st);
   int pr = ws.prof ? ws.prof->begin(KID_PACK, st) : -1;
   pack_kernel<<<Q, kThreads, 0, st>>>(im, K, KW, NC, bits, seg_base, pxoff, as<float>(ws.packed),
                                       z, 0, nonfinite);
   TRY(cudaGetLastError());
   if (ws.prof) ws.prof->end(pr, st);
 
-  if (ws.max_smem == 0) {
-    int dev;
-    TRY(cudaGetDevice(&dev));
-    TRY(cudaDeviceGetAttribute(&ws.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  }
   const bool pipe_ok = tc_pipe_supported(K, s, ws.max_smem);
   const int fin_grid = std::min(Q, ws.sm_count * 16);  // finalize: blocks over row items
   // launch geometry of the single-stage kernels (several CTAs per SM)
@@ -1059,29 +1290,7 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
     gk.Q = Q;
     gk.variant = variant;
     gk.iters = rem;
-    GraphSlot *slot = nullptr;
-    for (GraphSlot &g : ws.graphs_cached)
-      if (g.exec && std::memcmp(&gk, &g.key, sizeof gk) == 0) slot = &g;
-    if (!slot) {
-      // capture into the least recently used slot
-      slot = &ws.graphs_cached[0];
-      for (GraphSlot &g : ws.graphs_cached)
-        if (!g.exec || g.used < slot->used) slot = &g;
-      if (slot->exec) cudaGraphExecDestroy(slot->exec);
-      slot->exec = nullptr;
-      cudaGraph_t g = nullptr;
-      TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      cudaError_t err = cudaSuccess;
-      for (int it = 0; it < rem && err == cudaSuccess; ++it) err = iteration(variant);
-      cudaError_t e2 = cudaStreamEndCapture(st, &g);
-      if (err == cudaSuccess) err = e2;
-      if (err == cudaSuccess) err = cudaGraphInstantiate(&slot->exec, g, 0);
-      if (g) cudaGraphDestroy(g);
-      TRY(err);
-      slot->key = gk;
-    }
-    slot->used = ++ws.graph_clock;
-    TRY(cudaGraphLaunch(slot->exec, st));
+    TRY(replay_graph(ws, gk, rem, [&](int) { return iteration(variant); }, st));
   } else {
     for (int it = 0; it < rem; ++it) TRY(iteration(variant));
   }

@@ -19,13 +19,14 @@ enum KernelId {
   KID_ADJ_TC,
   KID_UNPACK,
   KID_SCREEN,
+  KID_FUSED,
   KID_COUNT
 };
 
 inline const char *kernel_name(int id) {
   static const char *names[KID_COUNT] = {"mask",     "power",    "synth_fp32", "adjoint_fp32",
                                          "pack",     "synth_tc", "finalize_r", "adj_tc",
-                                         "unpack",   "screen"};
+                                         "unpack",   "screen",   "fused"};
   return (id >= 0 && id < KID_COUNT) ? names[id] : "";
 }
 

@@ -437,7 +437,7 @@ scsc_status check_cfg(scsc_ctx *ctx, const scsc_config *c) {
   if (c->prec != SCSC_FP32 && c->prec != SCSC_BF16)
     return fail(ctx, SCSC_EINVAL, "unknown precision %d", (int)c->prec);
   if (c->flags & ~(SCSC_FLAG_PER_IMAGE | SCSC_FLAG_NO_GRAPH | SCSC_FLAG_NO_AUTOTUNE |
-                   SCSC_FLAG_UNSAMPLED_KEEP))
+                   SCSC_FLAG_UNSAMPLED_KEEP | SCSC_FLAG_TWO_KERNEL))
     return fail(ctx, SCSC_EINVAL, "unknown flags 0x%x", c->flags);
   return SCSC_OK;
 }
@@ -460,6 +460,7 @@ scsc_status scsc_create(const scsc_config *cfg, void *cuda_stream, scsc_ctx **ou
   c->tc.prof = &c->prof;
   c->tc.graphs = (cfg->flags & SCSC_FLAG_NO_GRAPH) == 0;
   c->tc.autotune = (cfg->flags & SCSC_FLAG_NO_AUTOTUNE) == 0;
+  c->tc.fused = (cfg->flags & SCSC_FLAG_TWO_KERNEL) == 0;
   c->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   if (cudaGetDevice(&c->device) != cudaSuccess) {
     delete c;

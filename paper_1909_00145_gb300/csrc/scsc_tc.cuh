@@ -25,6 +25,7 @@ struct TuneKey {
 struct GraphKey {
   const void *bits, *seg_base, *pxoff, *packed, *bsyn, *badj, *xcore, *spill, *r, *err, *x, *prm,
       *item0, *off, *obs, *abuf;
+  const void *v16a, *v16b, *idx16, *xcore2, *spill2;  // fused path
   int64_t total_px;
   int n_images, K, s, Q, variant, iters;
 };
@@ -46,13 +47,16 @@ struct TcWorkspace {
   };
   Buf item0, seg_count, seg_base, pxoff, scan_blocks, packed, xcore, spill, r, badj, bsyn, err;
   Buf abuf;  // dense BF16 code tiles in the synthesis A-operand layout (pipelined kernels)
+  // fused path: BF16 packed codes (input / output iterate), their A-tile
+  // indices, and the second set of synthesis buffers
+  Buf v16[2], idx16, xcore2, spill2;
   std::vector<int> host_item0;  // cached row-item map of the last batch
   std::vector<int> host_H, host_W;
   int n_items = 0;
   int sm_count = 0;
   int max_smem = 0;
   Profiler *prof = nullptr;  // the owning context's profiler
-  bool autotune = true, graphs = true;
+  bool autotune = true, graphs = true, fused = true;
   std::map<TuneKey, int> tune;                       // chosen variant per key
   std::map<TuneKey, std::pair<float, float>> tune_ms;  // timings that chose it
   GraphSlot graphs_cached[kGraphSlots];

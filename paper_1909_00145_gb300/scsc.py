@@ -26,7 +26,8 @@ STATUS_NAMES = ["SCSC_OK", "SCSC_EINVAL", "SCSC_ENOMEM", "SCSC_ECUDA", "SCSC_ETI
                 "SCSC_ENONFINITE", "SCSC_EUNSUPPORTED"]
 SCSC_FP32, SCSC_BF16, SCSC_TF32 = 0, 1, 2
 SCSC_DICT_BATCH, SCSC_DICT_ONLINE, SCSC_DICT_BATCH_GS = 0, 1, 2
-SCSC_FLAG_PER_IMAGE, SCSC_FLAG_NO_GRAPH, SCSC_FLAG_NO_AUTOTUNE, SCSC_FLAG_UNSAMPLED_KEEP = 1, 2, 4, 8
+(SCSC_FLAG_PER_IMAGE, SCSC_FLAG_NO_GRAPH, SCSC_FLAG_NO_AUTOTUNE, SCSC_FLAG_UNSAMPLED_KEEP,
+ SCSC_FLAG_TWO_KERNEL) = 1, 2, 4, 8, 16
 
 
 class scsc_config(ctypes.Structure):

@@ -47,7 +47,7 @@ def test_library_is_built_for_sm103a():
 def test_config_validation_happens_on_the_host():
     L = scsc.lib()
     bad = [dict(K=0), dict(K=600), dict(s=4), dict(s=13), dict(lam=0.0), dict(p=(3, 2)),
-           dict(p=(1, 0)), dict(step=-1.0), dict(flags=16), dict(prec=3)]
+           dict(p=(1, 0)), dict(step=-1.0), dict(flags=32), dict(prec=3)]
     for kw in bad:
         args = dict(K=16, s=11, lam=1.0, p=(1, 2), step=0.0, flags=0, prec=0)
         args.update(kw)
