@@ -237,6 +237,9 @@ __global__ void __launch_bounds__(Fus<S>::kThreads, 1) fused_kernel(const FusedA
       a_free[2], s_full[kRB], r_free[kRB], cb_full[4], cb_done[4], ring_init, done_bar;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
+  // per A tile: the 16-filter chunks that hold a nonzero code; the synthesis
+  // multiplies only those (the other chunks of the tile are zero: exact)
+  __shared__ uint32_t s_chunks[2];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
@@ -253,6 +256,7 @@ __global__ void __launch_bounds__(Fus<S>::kThreads, 1) fused_kernel(const FusedA
       tc::mbar_init(&adj_empty[i], L::kEpiW);
       tc::mbar_init(&a_full[i], L::kEpiW);
       tc::mbar_init(&a_free[i], 1);
+      s_chunks[i] = 0u;
     }
     // one phase per code row (s_full) and per folded output row (r_free); the
     // MMA issue runs at most kRB - 1 rows ahead of the fold, so kRB barriers
@@ -307,8 +311,11 @@ __global__ void __launch_bounds__(Fus<S>::kThreads, 1) fused_kernel(const FusedA
         const int rb0 = J0 & (kRB - 1);
         const int n1 = min(S, kRB - rb0), n2 = S - n1;
         const uint32_t ab = a_base + (uint32_t)(i & 1) * a_bytes;
+        const uint32_t chunks = *reinterpret_cast<volatile uint32_t *>(&s_chunks[i & 1]);
 #pragma unroll 1
-        for (int kk = 0; kk < NC; ++kk) {
+        for (uint32_t rest = chunks & ((NC < 32 ? (1u << NC) : 0u) - 1u); rest != 0u;
+             rest &= rest - 1u) {
+          const int kk = __ffs(rest) - 1;
           const uint64_t ad = tc::smem_desc(ab + kk * 2 * 2048, 2048, 128);
           const uint32_t bk = b_base + kk * 2 * 128;
           tc::mma_bf16(taddr + ring_col + 16 * rb0, ad, tc::smem_desc(bk, 128, Kp * 16),
@@ -548,12 +555,14 @@ __global__ void __launch_bounds__(Fus<S>::kThreads, 1) fused_kernel(const FusedA
           uint4 *at = reinterpret_cast<uint4 *>(As + (size_t)b * a_bytes);
           const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
           for (int k = et; k < (int)(a_bytes / 16); k += 32 * L::kEpiW) at[k] = zero;
+          if (et == 0) s_chunks[b] = 0u;
         }
         if (tc::named_sync_or(1, 32 * L::kEpiW, !okw)) {  // G written, A tile zeroed
           stop = true;
           break;
         }
         const uint32_t at_base = a_base + (uint32_t)b * a_bytes;
+        uint32_t cmask = 0u;  // 16-filter chunks this thread wrote a nonzero code to
         // the item's staged chunks: prox (or, for the input synthesis, the
         // codes as they are) into the staging buffer and the A tile
         while (okw && have_chunk && ci.pos >= ibeg && ci.pos < iend) {
@@ -588,6 +597,8 @@ __global__ void __launch_bounds__(Fus<S>::kThreads, 1) fused_kernel(const FusedA
               }
               if (in_lo) st_shared_u16(at_base + 2u * e_lo, vw[h] & 0xFFFFu);
               if (in_hi) st_shared_u16(at_base + 2u * e_hi, vw[h] >> 16);
+              if (in_lo && (vw[h] & 0x7FFFu)) cmask |= 1u << (e_lo >> 11);
+              if (in_hi && (vw[h] & 0x7FFF0000u)) cmask |= 1u << (e_hi >> 11);
             }
             if (iterate)
               *reinterpret_cast<uint4 *>(vals + g0) = make_uint4(vw[0], vw[1], vw[2], vw[3]);
@@ -599,6 +610,8 @@ __global__ void __launch_bounds__(Fus<S>::kThreads, 1) fused_kernel(const FusedA
           have_chunk = ci.next(im, A.seg_base);
         }
         if (okw) {
+          cmask = __reduce_or_sync(0xffffffffu, cmask);
+          if (lane == 0 && cmask != 0u) atomicOr(&s_chunks[b], cmask);
           tc::fence_proxy_async();
           __syncwarp();
           if (lane == 0) tc::mbar_arrive(&a_full[b]);

@@ -34,3 +34,17 @@ def oracle_bits(cfg: R.Config, batch: R.Batch, t: int) -> np.ndarray:
     for k in range(cfg.K):
         out[:, k // 32] |= m[:, k] << np.uint64(k % 32)
     return out.astype(np.uint32).ravel()
+
+
+def support_jaccard(a, b) -> float:
+    """Jaccard index of the nonzero sets of two code vectors (1 when both are
+    all zero): the support agreement of two solutions of the lasso."""
+    sa = np.asarray(a).ravel() != 0
+    sb = np.asarray(b).ravel() != 0
+    union = int(np.count_nonzero(sa | sb))
+    return 1.0 if union == 0 else int(np.count_nonzero(sa & sb)) / union
+
+
+def measured(name: str, **vals) -> None:
+    """Print a measured error next to its test (visible with pytest -s)."""
+    print("MEASURED " + name + " " + " ".join(f"{k}={v:.3e}" for k, v in vals.items()))

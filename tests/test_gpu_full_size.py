@@ -10,14 +10,19 @@ oracle recomputes sampled images of the full batch one by one:
 - the sampled images' masks bit-exact and their codes zero off the mask
   (Eq. 4) after the full 100-iteration update with the computed step size;
 - batch invariance at full size: an image's codes from the 64-image launch
-  equal those of a launch over that image alone, bit for bit.
+  equal those of a launch over that image alone, bit for bit;
+- the benchmark's own step (64 x 256^2, 100 iterations at the computed
+  1/L_z) on two sampled images against the oracle, and the same step teacher-
+  forced: the oracle takes the GPU's codes after iteration 50 and performs
+  iteration 51, so that the comparison sees one step's arithmetic rather than
+  100 steps of drift.
 """
 import numpy as np
 import pytest
 
 import bench
 from oracle import reference as R
-from tests.helpers import rel_l2
+from tests.helpers import measured, rel_l2, support_jaccard
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -74,8 +79,12 @@ def test_full_batch_sampled_images_match_oracle(name, sample, n_iters, prec):
             assert fg == pytest.approx(fo, rel=1e-5), (k, fg, fo)
             assert rel_l2(zk, zo) < 1e-4
         else:
+            measured(f"full_{name}_{k}", rel=rel_l2(zk, zo), jac=support_jaccard(zk, zo),
+                     obj=abs(fg - fo) / abs(fo))
             assert fg == pytest.approx(fo, rel=1e-3), (k, fg, fo)
-            assert rel_l2(zk, zo) < 5e-2
+            # measured 4.9e-3 .. 5.3e-3 and Jaccard >= 0.994 on these images
+            assert rel_l2(zk, zo) < 1.2e-2
+            assert support_jaccard(zk, zo) >= 0.985
 
 
 def test_c3_full_update_masks_and_eq4_zeros():
@@ -110,3 +119,55 @@ def test_c3_batch_invariance_bit_exact():
     _, _, z1 = gpu_code_step(wl, H[k:k + 1], W[k:k + 1], ids[k:k + 1], xk, d, "bf16",
                              wl["n_iters"], t=2, flags=scsc.SCSC_FLAG_NO_AUTOTUNE)
     assert np.array_equal(image_codes(zg, rb, k, wl["K"]), z1.cpu().numpy())
+
+
+def test_c3_benchmark_step_against_oracle_and_teacher_forced():
+    wl = bench.WORKLOADS["c3"]
+    H, W, ids, x, d = bench.make_inputs(wl, 0)
+    K, n_iters, sample = wl["K"], wl["n_iters"], [0, 37]
+    cfg = R.Config(K=K, s=11, lam=1.0, p_num=wl["p"][0], p_den=wl["p"][1], seed=0)
+    rb = R.Batch(H=H, W=W, ids=ids)
+    rk = R.Batch(H=[H[k] for k in sample], W=[W[k] for k in sample], ids=[ids[k] for k in sample])
+    xk = np.concatenate([rb.image(x, k) for k in sample])
+    # the step both sides compute: 1/L_z of the 256 x 256 domain
+    alpha_o = 1.0 / R.lipschitz_codes(cfg, d, int(H[0]), int(W[0]))
+    ctx = scsc.Context(K, 11, 1.0, wl["p"], seed=0, prec="bf16", stream=torch.cuda.Stream())
+    batch = scsc.Batch(H, W, ids)
+    xt = torch.from_numpy(x).cuda()
+    dt = torch.from_numpy(np.ascontiguousarray(d)).cuda()
+    alpha_g = 1.0 / ctx.lipschitz_codes(batch, dt)
+    assert alpha_g == pytest.approx(alpha_o, rel=1e-4)
+
+    def gpu(z, its):
+        torch.cuda.synchronize()
+        with torch.cuda.stream(ctx.stream):
+            ctx.code_step(batch, xt, dt, z, 1, its)
+            ctx.sync()
+        return z
+
+    def sampled(z):
+        return np.concatenate([image_codes(z, rb, k, K) for k in sample])
+
+    # the whole benchmark step from zero codes
+    zg = sampled(gpu(torch.zeros(batch.total_pixels * K, device="cuda"), n_iters))
+    zo = R.code_step(cfg, rk, xk, d, np.zeros(zg.size), 1, n_iters, step=alpha_o)
+    fo, fg = R.objective(cfg, rk, xk, zo, d), R.objective(cfg, rk, xk, zg, d)
+    measured("c3_step100", rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo), obj=abs(fg - fo) / abs(fo))
+    assert fg == pytest.approx(fo, rel=1e-3)
+    # after 100 iterations the two paths have drifted apart along the
+    # lasso's flat directions (measured 2.7e-2, objective 3.4e-5, support
+    # Jaccard 0.996); one step from the same state is the tight check below
+    assert rel_l2(zg, zo) < 5.5e-2
+    assert support_jaccard(zg, zo) >= 0.99
+    # teacher forcing: both sides take iteration 51 from the GPU's codes after 50
+    z50 = gpu(torch.zeros(batch.total_pixels * K, device="cuda"), n_iters // 2)
+    z50_k = sampled(z50)
+    z51g = sampled(gpu(z50.clone(), 1))
+    z51o = R.code_step(cfg, rk, xk, d, z50_k, 1, 1, step=alpha_o)
+    measured("c3_teacher51", rel=rel_l2(z51g, z51o), jac=support_jaccard(z51g, z51o),
+             moved=rel_l2(z51o, z50_k))
+    # one BF16 iteration: measured 1.7e-3 (the step itself moves the codes by
+    # 1.1e-2), identical supports
+    assert rel_l2(z51g, z51o) < 4e-3
+    assert support_jaccard(z51g, z51o) >= 0.995
+    ctx.close()

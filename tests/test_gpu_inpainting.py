@@ -10,7 +10,7 @@ import pytest
 import bench
 from oracle import reference as R
 from paper_1909_00145_gb300 import inputs as I
-from tests.helpers import make_case, rel_l2
+from tests.helpers import make_case, measured, rel_l2, support_jaccard
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -43,7 +43,13 @@ def test_observed_code_step_matches_oracle(prec, p):
     fg = ctx.objective_observed(b, xt, z, dt, ot)
     tol = 1e-5 if prec == "fp32" else 1e-3
     assert fg == pytest.approx(fo, rel=tol)
-    assert rel_l2(z.cpu().numpy(), zo) < (1e-4 if prec == "fp32" else 5e-2)
+    zg = z.cpu().numpy()
+    measured("inpaint_" + prec, rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo))
+    if prec == "fp32":
+        assert rel_l2(zg, zo) < 1e-4
+    else:
+        assert rel_l2(zg, zo) < 1.2e-2  # measured 4.6e-3 .. 5.0e-3
+        assert support_jaccard(zg, zo) >= 0.985
     # the unobserved pixels really are out of the data term: the plain
     # objective of the same codes is larger
     assert ctx.objective(b, xt, z, dt) > fg
@@ -95,4 +101,11 @@ def test_inpainting_workload_sampled_image(prec):
     fo = R.objective_observed(cfg, rk, xk, zo, d, ok)
     fg = R.objective_observed(cfg, rk, xk, zk, d, ok)
     assert fg == pytest.approx(fo, rel=1e-5 if prec == "fp32" else 1e-3)
-    assert rel_l2(zk, zo) < (1e-4 if prec == "fp32" else 5e-2)
+    measured("inpaint_full_" + prec, rel=rel_l2(zk, zo), jac=support_jaccard(zk, zo))
+    if prec == "fp32":
+        assert rel_l2(zk, zo) < 1e-4
+    else:
+        # the longer run drifts further than the 12-iteration case above:
+        # measured 1.1e-2, Jaccard 0.995
+        assert rel_l2(zk, zo) < 2.5e-2
+        assert support_jaccard(zk, zo) >= 0.985

@@ -1,17 +1,30 @@
 """GPU parity: the CUDA library against the FP64 oracle on the same seeded
 inputs.  Masks are compared bit for bit; floating point within the stated
 tolerances (FP32 path: objective 1e-5 rel, codes/filters 1e-4 rel L2; BF16
-path: objective 1e-3 rel)."""
+path: objective 1e-3 rel, codes 1e-2 rel L2 (about twice the largest error
+measured on these cases, 5.3e-3: a few BF16 roundings of u = 2^-9 each) and a
+nonzero-support Jaccard index of at least 0.985 (measured >= 0.993)).
+
+BF16_CODES and BF16_SUPPORT hold those two bounds."""
 import numpy as np
 import pytest
 
 from oracle import reference as R
-from tests.helpers import make_case, oracle_bits, rel_l2
+from tests.helpers import make_case, measured, oracle_bits, rel_l2, support_jaccard
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_1909_00145_gb300 import scsc  # noqa: E402
+
+
+BF16_CODES = 1e-2
+BF16_SUPPORT = 0.985
+
+
+def check_bf16_codes(zg, zo, tol=BF16_CODES):
+    assert rel_l2(zg, zo) < tol
+    assert support_jaccard(zg, zo) >= BF16_SUPPORT
 
 
 def dev(a, dtype=torch.float32):
@@ -156,8 +169,9 @@ def test_code_step_c1_fp32():
 
 def test_code_step_c1_bf16():
     zg, zo, fg, fo, _ = run_code_step("bf16", 16, 11, [100], [100], (1, 2), 20)
+    measured("c1_bf16", rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo), obj=abs(fg - fo) / abs(fo))
     assert fg == pytest.approx(fo, rel=1e-3)
-    assert rel_l2(zg, zo) < 5e-2
+    check_bf16_codes(zg, zo)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -166,9 +180,13 @@ def test_code_step_ragged_batch(prec):
     and short images; K not a multiple of 16; s = 5."""
     H, W = [37, 20, 3, 64], [131, 260, 5, 64]
     zg, zo, fg, fo, _ = run_code_step(prec, 20, 5, H, W, (1, 3), 12, seed=3, lam=0.5)
+    measured("ragged_" + prec, rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo), obj=abs(fg - fo) / abs(fo))
     tol = 1e-5 if prec == "fp32" else 1e-3
     assert fg == pytest.approx(fo, rel=tol)
-    assert rel_l2(zg, zo) < (1e-4 if prec == "fp32" else 5e-2)
+    if prec == "fp32":
+        assert rel_l2(zg, zo) < 1e-4
+    else:
+        check_bf16_codes(zg, zo)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -176,7 +194,12 @@ def test_code_step_warm_start_and_p_one(prec):
     K, s, H, W = 8, 7, [30], [140]
     x, d, z = make_case(H, W, K, s, seed=8, code_density=0.2)
     zg, zo, fg, fo, _ = run_code_step(prec, K, s, H, W, (1, 1), 5, t=3, seed=8, lam=0.3, warm=z)
+    measured("warm_p1_" + prec, rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo), obj=abs(fg - fo) / abs(fo))
     assert fg == pytest.approx(fo, rel=1e-5 if prec == "fp32" else 1e-3)
+    if prec == "fp32":
+        assert rel_l2(zg, zo) < 1e-4
+    else:
+        check_bf16_codes(zg, zo)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -192,7 +215,12 @@ def test_code_step_p_zero_and_zero_iterations(prec):
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_code_step_fixed_step(prec):
     zg, zo, fg, fo, _ = run_code_step(prec, 12, 11, [40], [150], (1, 4), 8, step=0.02, lam=0.8)
+    measured("fixed_step_" + prec, rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo), obj=abs(fg - fo) / abs(fo))
     assert fg == pytest.approx(fo, rel=1e-5 if prec == "fp32" else 1e-3)
+    if prec == "fp32":
+        assert rel_l2(zg, zo) < 1e-4
+    else:
+        check_bf16_codes(zg, zo)
 
 
 # ------------------------------------------------------------------ dictionary steps
@@ -239,10 +267,35 @@ def test_dict_step_online_fp32_and_state_roundtrip():
     assert torch.equal(d_saved, dt)
 
 
+def test_dict_step_online_k64_s11():
+    """Eq. 7-8 at the filter size of the paper's runs (K = 64, s = 11, so the
+    surrogate C is 7744 x 7744) on small images: a stream of three mini-
+    batches, each step against the oracle's."""
+    K, s, H, W = 64, 11, [14, 18], [20, 16]
+    cfg = R.Config(K=K, s=s, seed=9)
+    st = R.OnlineState(cfg)
+    ctx = scsc.Context(K, s, seed=9)
+    b = scsc.Batch(H, W)
+    rb = R.Batch(H=H, W=W, ids=[0, 1])
+    _, d, _ = make_case(H, W, K, s, seed=31)
+    dt = dev(d)
+    d_o = d.astype(np.float64).ravel()
+    for t in range(1, 4):
+        x, _, z = make_case(H, W, K, s, seed=40 + t, code_density=0.02)
+        st.update(rb, x, z)
+        d_o = st.dict_step(d_o)
+        ctx.dict_step(b, dev(x), dev(z), dt, scsc.SCSC_DICT_ONLINE, t)
+        measured(f"online_k64_t{t}", rel=rel_l2(host(dt), d_o))
+        assert rel_l2(host(dt), d_o) < 1e-6  # measured <= 6.2e-8
+    assert np.all(np.linalg.norm(host(dt).reshape(K, -1), axis=1) <= 1 + 1e-6)
+
+
 def test_code_step_bf16_large_k_fallback_kernels():
     """128 < K <= 256 runs the single-stage tensor kernels."""
     zg, zo, fg, fo, _ = run_code_step("bf16", 150, 5, [20, 9], [70, 140], (1, 4), 6, seed=4, lam=0.6)
+    measured("large_k", rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo), obj=abs(fg - fo) / abs(fo))
     assert fg == pytest.approx(fo, rel=1e-3)
+    check_bf16_codes(zg, zo)
 
 
 @pytest.mark.parametrize("K", [128, 113, 1])
@@ -252,8 +305,9 @@ def test_code_step_pipelined_limits(K):
     and a single filter."""
     zg, zo, fg, fo, _ = run_code_step("bf16", K, 11, [40, 30], [140, 70], (1, 1), 5, seed=12,
                                       lam=0.8)
+    measured(f"limits_{K}", rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo), obj=abs(fg - fo) / abs(fo))
     assert fg == pytest.approx(fo, rel=1e-3)
-    assert rel_l2(zg, zo) < 5e-2
+    check_bf16_codes(zg, zo)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
@@ -262,8 +316,12 @@ def test_code_step_many_items_per_cta(prec):
     persistent CTA crosses strip and image boundaries."""
     H, W = [50] * 24, [260] * 24
     zg, zo, fg, fo, _ = run_code_step(prec, 32, 7, H, W, (1, 4), 6, seed=6, lam=0.7)
+    measured("many_items_" + prec, rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo), obj=abs(fg - fo) / abs(fo))
     assert fg == pytest.approx(fo, rel=1e-5 if prec == "fp32" else 1e-3)
-    assert rel_l2(zg, zo) < (1e-4 if prec == "fp32" else 5e-2)
+    if prec == "fp32":
+        assert rel_l2(zg, zo) < 1e-4
+    else:
+        check_bf16_codes(zg, zo)
 
 
 @pytest.mark.parametrize("K,s,H,W", [(12, 11, [40, 33], [50, 61]), (20, 5, [37, 64], [131, 64]),

@@ -11,7 +11,7 @@ import pytest
 
 import bench
 from oracle import reference as R
-from tests.helpers import make_case, oracle_bits, rel_l2
+from tests.helpers import make_case, measured, oracle_bits, rel_l2, support_jaccard
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -134,7 +134,10 @@ def test_code_step_screened_matches_oracle(prec):
         # survivors agree up to coordinates decided inside the rounding band
         assert np.abs(kept - [int(rb.image(mo, n, K).sum()) for n in range(rb.n)]).max() <= 2
     else:
-        assert rel_l2(zg, zo) < 5e-2
+        measured("screen_bf16", rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo))
+        # 60 iterations: measured 1.1e-2, identical supports
+        assert rel_l2(zg, zo) < 2.5e-2
+        assert support_jaccard(zg, zo) >= 0.985
         assert fg == pytest.approx(fo, rel=1e-3)
         assert abs(int(kept.sum()) - int(mo.sum())) <= 0.02 * m0.sum()
     assert mo.sum() < 0.9 * m0.sum()  # the oracle's run removed coordinates
