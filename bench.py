@@ -174,14 +174,17 @@ def measured_traffic(kernel: str, npx: int):
     """DRAM bytes per launch of `kernel` from the committed ncu counters of the
     small profiling workload, scaled by pixels; None if the kernel source's
     code has changed since the counters were taken."""
-    names = {"adj_tc": "adj2_kernel", "synth_tc": "syn2_kernel"}
+    names = {"adj_tc": ("tc_kernels_prof_workload_counters.json", "adj2_kernel"),
+             "synth_tc": ("tc_kernels_prof_workload_counters.json", "syn2_kernel"),
+             "fused": ("fused_kernel_prof_workload_counters.json", "fused_kernel")}
     try:
-        with open(os.path.join(ROOT, "profiles", "tc_kernels_prof_workload_counters.json")) as f:
+        fname, kname = names[kernel]
+        with open(os.path.join(ROOT, "profiles", fname)) as f:
             c = json.load(f)
         with open(os.path.join(ROOT, c["source"])) as f:
             if source_code_sha1(f.read()) != c["source_code_sha1"]:
                 return None
-        k = c["kernels"][names[kernel]]
+        k = c["kernels"][kname]
         return k["dram_bytes_per_launch"] * npx / c["workload_pixels"]
     except (OSError, KeyError, ValueError):
         return None

@@ -54,6 +54,33 @@ scsc_status scsc_diag_profile(scsc_ctx *ctx, int enable);
 scsc_status scsc_diag_kernel_time(scsc_ctx *ctx, const char *name, double *total_ms,
                                   int *launches);
 
+/* scsc_diag_mma_rate times 64 back-to-back tcgen05 MMAs of shape M = 128,
+ * K = 16 and the given N (a multiple of 16 in [16, 256]) issued by one
+ * thread of one CTA, on zero BF16 operands in shared memory, after one
+ * untimed round.  layout 0: both operands K-major (no swizzle); 1: A is the
+ * overlapping Toeplitz view the adjoint uses (core-matrix strides of 128
+ * bytes in both directions), B K-major; 2: A K-major, B MN-major (the
+ * synthesis's filter operand).  *issue_cycles (may be NULL) receives the SM
+ * cycles per MMA until the last one was issued, *complete_cycles the cycles
+ * per MMA until their completion barrier.  Runs on the legacy default stream
+ * and synchronises the device.  Returns SCSC_OK, SCSC_EINVAL for a bad N,
+ * layout or NULL complete_cycles, SCSC_ENOMEM, SCSC_ECUDA, or SCSC_ETIMEOUT
+ * if the completion barrier was not reached within one second.  The paper
+ * has no counterpart: this measures the tensor core's rate for the MMA
+ * shapes the code update issues. */
+scsc_status scsc_diag_mma_rate(int N, int layout, double *issue_cycles, double *complete_cycles);
+
+/* scsc_diag_ffma_peak measures the FP32 fused multiply-add rate of the
+ * current device: a SIMT kernel of independent FMA chains (4 blocks of 512
+ * threads per SM), the fastest of five launches timed with CUDA events after
+ * one warm-up launch on the legacy default stream.  *tflops receives
+ * 2 x FMAs / time in TFLOP/s, *ms (may be NULL) the kernel time.  This is the
+ * denominator of the plain FP32 path's roofline fraction, whose synthesis and
+ * adjoint are FMA-bound.  Returns SCSC_OK, SCSC_EINVAL for a NULL tflops,
+ * SCSC_ENOMEM if its output buffer cannot be allocated, SCSC_ECUDA on a CUDA
+ * error.  The paper has no counterpart: this measures the hardware. */
+scsc_status scsc_diag_ffma_peak(double *tflops, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1315,7 +1315,77 @@ __global__ void selftest_wait_kernel(uint64_t limit_ns, int *err) {
     if (!tc::mbar_wait_bounded(&bar, 0, limit_ns)) atomicExch(err, 1);
   }
 }
+// The issue and completion rate of back-to-back tcgen05 MMAs of M = 128,
+// K = 16 and the given N from one thread, on zero operands (the rate does not
+// depend on the values).  layout 0: A K-major (8 x 16-byte core matrices, 256
+// bytes apart along M), B K-major; 1: A the overlapping Toeplitz view of the
+// adjoint (core matrices 128 bytes apart in both directions), B K-major;
+// 2: A K-major, B MN-major (the synthesis's filter operand).  Every operand
+// lies inside the 24 KB zeroed here: A spans at most 4 KB, B at most 8 KB at
+// N = 256.  out[0]: cycles to issue the timed MMAs, out[1]: cycles until
+// their completion barrier.
+__global__ void __launch_bounds__(kThreads) selftest_mma_rate_kernel(int N, int layout, int reps,
+                                                                     long long *out, int *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&tmem_base, 256);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    tc::fence_mbar_init();
+  }
+  for (int t = tid; t < 24 * 1024 / 16; t += kThreads)
+    reinterpret_cast<uint4 *>(smem)[t] = make_uint4(0u, 0u, 0u, 0u);
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t taddr = tmem_base;
+  bool ok = true;
+  if (tid == 0) {
+    const uint32_t a0 = tc::smem_u32(smem), b0 = a0 + 16 * 1024;
+    const uint64_t ad = layout == 1 ? tc::smem_desc(a0, 128, 128) : tc::smem_desc(a0, 128, 256);
+    const uint64_t bd = layout == 2 ? tc::smem_desc(b0, 128, 256) : tc::smem_desc(b0, N * 16, 128);
+    const uint32_t idesc = layout == 2 ? tc::idesc_bf16_f32_bmn(128, N) : tc::idesc_bf16_f32(128, N);
+    // one untimed round, then the timed one
+    for (int round = 0; round < 2 && ok; ++round) {
+      const long long t0 = clock64();
+      for (int r = 0; r < reps; ++r) tc::mma_bf16(taddr, ad, bd, idesc, r > 0 ? 1u : 0u);
+      const long long t1 = clock64();
+      tc::mma_commit(&mbar);
+      ok = tc::mbar_wait_bounded(&mbar, (uint32_t)round, kWaitNs);
+      const long long t2 = clock64();
+      out[0] = t1 - t0;
+      out[1] = t2 - t0;
+      if (!ok) {
+        // the MMAs in flight finish (bounded) before the TMEM is released
+        atomicExch(err, 1);
+        tc::mbar_wait_bounded(&mbar, (uint32_t)round, kWaitNs);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(taddr, 256);
+  }
+}
+
 }  // namespace
+
+cudaError_t tc_selftest_mma_rate(int N, int layout, int reps, long long *out, int *err,
+                                 cudaStream_t st) {
+  if (N < 16 || N > 256 || N % 16 != 0 || layout < 0 || layout > 2 || reps < 1 || reps > 4096)
+    return cudaErrorInvalidValue;
+  selftest_mma_rate_kernel<<<1, kThreads, 1024 + 24 * 1024, st>>>(N, layout, reps, out, err);
+  return cudaGetLastError();
+}
 
 cudaError_t tc_selftest_wait(uint64_t limit_ns, int *err, cudaStream_t st) {
   selftest_wait_kernel<<<1, 32, 0, st>>>(limit_ns, err);

@@ -1097,6 +1097,37 @@ scsc_status scsc_diag_tc_gemm_mn(int N, const float *A_dev, const float *B_dev, 
   return s;
 }
 
+scsc_status scsc_diag_mma_rate(int N, int layout, double *issue_cycles, double *complete_cycles) {
+  if (!complete_cycles || N < 16 || N > 256 || N % 16 != 0 || layout < 0 || layout > 2)
+    return SCSC_EINVAL;
+  const int reps = 64;
+  int *err = nullptr;
+  long long *out = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return SCSC_ENOMEM;
+  if (cudaMalloc(&out, 2 * sizeof(long long)) != cudaSuccess) {
+    cudaFree(err);
+    return SCSC_ENOMEM;
+  }
+  scsc_status s = SCSC_OK;
+  long long h[2] = {0, 0};
+  int word = 0;
+  if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
+      tc_selftest_mma_rate(N, layout, reps, out, err, nullptr) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(&word, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(h, out, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    s = SCSC_ECUDA;
+  } else if (word) {
+    s = SCSC_ETIMEOUT;
+  } else {
+    if (issue_cycles) *issue_cycles = (double)h[0] / reps;
+    *complete_cycles = (double)h[1] / reps;
+  }
+  cudaFree(out);
+  cudaFree(err);
+  return s;
+}
+
 scsc_status scsc_diag_wait_timeout(double limit_ms) {
   if (!(limit_ms > 0.0 && limit_ms <= 1000.0)) return SCSC_EINVAL;
   int *err = nullptr;

@@ -92,6 +92,8 @@ cudaError_t tc_selftest_gemm_mn(int N, const float *A, const float *B, float *D,
                                 int *err, cudaStream_t st);
 // One bounded mbarrier wait that nothing completes: sets *err after limit_ns.
 cudaError_t tc_selftest_wait(uint64_t limit_ns, int *err, cudaStream_t st);
+cudaError_t tc_selftest_mma_rate(int N, int layout, int reps, long long *out, int *err,
+                                 cudaStream_t st);
 
 // Pipelined tensor kernels (kernels_tc_pipe.cu): K <= 128 and shared memory
 // within `max_smem` bytes per block.

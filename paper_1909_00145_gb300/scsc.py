@@ -88,6 +88,8 @@ _SIGNATURES = {
     "scsc_diag_tc_gemm": [c_int, c_void_p, c_void_p, c_void_p],
     "scsc_diag_tc_gemm_mn": [c_int, c_void_p, c_void_p, c_void_p, c_int],
     "scsc_diag_wait_timeout": [c_double],
+    "scsc_diag_ffma_peak": [ctypes.POINTER(c_double), ctypes.POINTER(c_double)],
+    "scsc_diag_mma_rate": [c_int, c_int, ctypes.POINTER(c_double), ctypes.POINTER(c_double)],
     "scsc_objective_noalloc": [ctypes.POINTER(scsc_config), c_int, c_int, c_int, c_void_p,
                                c_void_p, c_void_p, c_void_p, c_void_p],
     "scsc_diag_profile": [c_void_p, c_int],
@@ -485,6 +487,22 @@ def scsc_diag_wait_timeout(limit_ms: float = 20.0) -> int:
     """Run the kernels' bounded mbarrier wait on a barrier that nothing
     completes; returns the status (SCSC_ETIMEOUT when the wait ran out)."""
     return int(lib().scsc_diag_wait_timeout(float(limit_ms)))
+
+
+def scsc_diag_ffma_peak():
+    """(TFLOP/s, ms): the measured FP32 FMA rate of the current device."""
+    tf, ms = c_double(), c_double()
+    _check(lib().scsc_diag_ffma_peak(ctypes.byref(tf), ctypes.byref(ms)), None,
+           "scsc_diag_ffma_peak")
+    return tf.value, ms.value
+
+
+def scsc_diag_mma_rate(N: int, layout: int = 0):
+    """(issue, completion) SM cycles per tcgen05 MMA of 128 x N x 16."""
+    iss, comp = c_double(), c_double()
+    _check(lib().scsc_diag_mma_rate(int(N), int(layout), ctypes.byref(iss), ctypes.byref(comp)),
+           None, "scsc_diag_mma_rate")
+    return iss.value, comp.value
 
 
 def scsc_diag_profile(ctx: Context, enable: bool = True) -> None:

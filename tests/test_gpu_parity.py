@@ -142,6 +142,29 @@ def test_step_size_operator_on_small_and_ragged_domains(s, H, W):
     assert L == pytest.approx(R.lipschitz_codes(cfg, d, H, W), rel=2e-5)
 
 
+def test_ffma_peak_is_plausible():
+    """The FP32 FMA rate that the plain path's roofline is quoted against:
+    128 FP32 lanes per SM, 2 flops per FMA; measured between half and 105 %
+    of that at a 2.1 GHz clock."""
+    tf, ms = scsc.scsc_diag_ffma_peak()
+    nominal = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * 2.1e9 / 1e12
+    assert 0.5 * nominal < tf < 1.05 * nominal, (tf, nominal)
+    assert ms > 0
+
+
+@pytest.mark.parametrize("layout", [0, 1, 2])
+def test_mma_rate_is_plausible(layout):
+    """tcgen05 MMA rate for the code update's shapes: never faster than the
+    dense BF16 peak of 8192 flop per SM cycle (N / 2 cycles for 128 x N x 16),
+    and the whole 64-MMA round completes within a few times that."""
+    for N in (16, 112, 176, 256):
+        issue, complete = scsc.scsc_diag_mma_rate(N, layout)
+        ideal = 2 * 128 * N * 16 / 8192
+        assert complete >= 0.95 * ideal, (N, complete)
+        assert complete < 8 * max(ideal, 16), (N, complete)
+        assert 0 < issue <= complete
+
+
 # ------------------------------------------------------------------ code step
 
 def run_code_step(prec, K, s, H, W, p, n_iters, t=1, seed=0, lam=1.0, warm=None, step=0.0):
