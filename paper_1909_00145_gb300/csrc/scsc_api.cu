@@ -101,6 +101,10 @@ struct scsc_ctx {
               ev_out[2] = {nullptr, nullptr};
   // tensor path
   TcWorkspace tc;
+  // the dictionary step's index of the nonzero codes: counts, offsets,
+  // pixel-major and filter-major entries (kernels_sparse.cu)
+  DevBuf sp_cpx, sp_ckt, sp_row, sp_kt, sp_scan, sp_pk, sp_pv, sp_kpix, sp_kimg, sp_kv;
+  bool sp_use = false;
   // online surrogates
   DevBuf C, B, Cd;
   uint64_t online_t = 0;
@@ -330,9 +334,86 @@ scsc_status power_iteration(scsc_ctx *ctx, int64_t n, uint64_t tag, Op &&apply, 
   return SCSC_OK;
 }
 
+constexpr int kSparseGroups = 8;  // partials per filter of the sparse gradient
+
+// Build the index of z's nonzero codes for the dictionary step's operators
+// and set ctx->sp_use.  The dense operators stay in use when the codes are
+// denser than 1/16 (where they are the faster ones), when a pixel index would
+// not fit in 32 bits, or inside a stream capture (the entry count is read
+// back to size the index).
+scsc_status build_sparse(scsc_ctx *ctx, const float *z) {
+  ctx->sp_use = false;
+  const BatchDev &b = ctx->batch.view;
+  const int K = ctx->cfg.K;
+  cudaStream_t st = ctx->stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CK(cudaStreamIsCapturing(st, &cap));
+  if (cap != cudaStreamCaptureStatusNone || b.total_px <= 0 || b.total_px >= INT32_MAX)
+    return SCSC_OK;
+  const int nt = sparse_tiles(b.total_px);
+  const int64_t nkt = (int64_t)K * nt;
+  CK(ctx->sp_cpx.ensure((size_t)b.total_px * 4));
+  CK(ctx->sp_ckt.ensure((size_t)nkt * 4));
+  CK(ctx->sp_row.ensure((size_t)(b.total_px + 1) * 8));
+  CK(ctx->sp_kt.ensure((size_t)(nkt + 1) * 8));
+  CK(ctx->sp_scan.ensure(std::max(sparse_scan_scratch(b.total_px), sparse_scan_scratch(nkt)) * 8));
+  CK(launch_sparse_count(b, K, z, ctx->sp_cpx.as<int>(), ctx->sp_ckt.as<int>(), st));
+  CK(launch_scan_counts(ctx->sp_cpx.as<int>(), b.total_px, ctx->sp_row.as<int64_t>(),
+                        ctx->sp_scan.as<int64_t>(), st));
+  CK(launch_scan_counts(ctx->sp_ckt.as<int>(), nkt, ctx->sp_kt.as<int64_t>(),
+                        ctx->sp_scan.as<int64_t>(), st));
+  int64_t nnz = 0;
+  CK(cudaMemcpyAsync(&nnz, ctx->sp_row.as<int64_t>() + b.total_px, sizeof nnz,
+                     cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (nnz * 16 > b.total_px * (int64_t)K) return SCSC_OK;
+  const size_t n1 = (size_t)std::max<int64_t>(nnz, 1);
+  CK(ctx->sp_pk.ensure(n1 * 4));
+  CK(ctx->sp_pv.ensure(n1 * 4));
+  CK(ctx->sp_kpix.ensure(n1 * 4));
+  CK(ctx->sp_kimg.ensure(n1 * 4));
+  CK(ctx->sp_kv.ensure(n1 * 4));
+  CK(launch_sparse_fill(b, K, z, ctx->sp_row.as<int64_t>(), ctx->sp_kt.as<int64_t>(),
+                        ctx->sp_pk.as<int>(), ctx->sp_pv.as<float>(), ctx->sp_kpix.as<int>(),
+                        ctx->sp_kimg.as<int>(), ctx->sp_kv.as<float>(), st));
+  ctx->sp_use = true;
+  return SCSC_OK;
+}
+
+// out = D z (minus x when given) with filters d, on the index when it is in use.
+scsc_status dict_synth(scsc_ctx *ctx, const float *d, const float *z, const float *x, float *out) {
+  const BatchDev &b = ctx->batch.view;
+  if (ctx->sp_use)
+    CK(launch_sparse_synth(b, ctx->cfg.K, ctx->cfg.s, d, ctx->sp_row.as<int64_t>(),
+                           ctx->sp_pk.as<int>(), ctx->sp_pv.as<float>(), x, out, ctx->stream));
+  else
+    CK(launch_synth_fp32(b, ctx->cfg.K, ctx->cfg.s, d, z, nullptr, x, out, ctx->stream));
+  return SCSC_OK;
+}
+
+// gsum = Z^T r (FP64), on the index when it is in use.
+scsc_status dict_gradient(scsc_ctx *ctx, const float *r, const float *z) {
+  if (!ctx->sp_use) return filter_gradient(ctx, r, z, nullptr);
+  const int K = ctx->cfg.K, M = M_of(ctx);
+  CK(ctx->gpart.ensure((size_t)kSparseGroups * K * M * 4));
+  CK(ctx->gsum.ensure((size_t)K * M * 8));
+  CK(launch_sparse_grad(ctx->batch.view, K, ctx->cfg.s, r, ctx->sp_kt.as<int64_t>(),
+                        ctx->sp_kpix.as<int>(), ctx->sp_kimg.as<int>(), ctx->sp_kv.as<float>(),
+                        ctx->gpart.as<float>(), kSparseGroups, ctx->stream));
+  CK(launch_reduce_partials(ctx->gpart.as<float>(), kSparseGroups, K * M, ctx->gsum.as<double>(),
+                            ctx->stream));
+  return SCSC_OK;
+}
+
 scsc_status apply_ztz(scsc_ctx *ctx, const float *z, const float *v, float *w) {
   const BatchDev &b = ctx->batch.view;
   const int K = ctx->cfg.K, M = M_of(ctx);
+  if (ctx->sp_use) {
+    CKS(dict_synth(ctx, v, z, nullptr, ctx->pix2.as<float>()));
+    CKS(dict_gradient(ctx, ctx->pix2.as<float>(), z));
+    CK(launch_double_to_float(ctx->gsum.as<double>(), w, K * M, ctx->stream));
+    return SCSC_OK;
+  }
   CK(launch_synth_fp32(b, K, ctx->cfg.s, v, z, nullptr, nullptr, ctx->pix2.as<float>(),
                        ctx->stream));
   CKS(filter_gradient(ctx, ctx->pix2.as<float>(), z, nullptr));
@@ -976,13 +1057,21 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
     CK(ctx->pix2.ensure((size_t)b.total_px * 4));
     CK(ctx->gsum.ensure((size_t)K * M * 8));
     CK(ctx->Cd.ensure((size_t)K * M * 8));
+    // the operators on the nonzero codes where they are sparse enough
+    CKS(build_sparse(ctx, z_dev));
     // r = D z - x, G = Z^T r (kept aside while the power iteration reuses gsum)
-    CK(launch_synth_fp32(b, K, s, d_dev, z_dev, nullptr, x_dev, ctx->r.as<float>(), st));
-    CKS(filter_gradient(ctx, ctx->r.as<float>(), z_dev, nullptr));
-    CK(cudaMemcpyAsync(ctx->Cd.p, ctx->gsum.p, (size_t)K * M * 8, cudaMemcpyDeviceToDevice, st));
-    CKS(power_iteration(ctx, (int64_t)K * M, kTagLd,
-                        [&](const float *u, float *w) { return apply_ztz(ctx, z_dev, u, w); }, 1,
-                        nullptr, 0.0));
+    scsc_status stt = dict_synth(ctx, d_dev, z_dev, x_dev, ctx->r.as<float>());
+    if (stt == SCSC_OK) stt = dict_gradient(ctx, ctx->r.as<float>(), z_dev);
+    if (stt == SCSC_OK &&
+        cudaMemcpyAsync(ctx->Cd.p, ctx->gsum.p, (size_t)K * M * 8, cudaMemcpyDeviceToDevice,
+                        st) != cudaSuccess)
+      stt = fail(ctx, SCSC_ECUDA, "copy of the gradient failed");
+    if (stt == SCSC_OK)
+      stt = power_iteration(
+          ctx, (int64_t)K * M, kTagLd,
+          [&](const float *u, float *w) { return apply_ztz(ctx, z_dev, u, w); }, 1, nullptr, 0.0);
+    ctx->sp_use = false;
+    CKS(stt);
     CK(launch_project_step(d_dev, nullptr, ctx->Cd.as<double>(), ctx->scal.as<double>() + 1, K, M,
                            st));
     return SCSC_OK;
@@ -991,9 +1080,12 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
     CK(ctx->r.ensure((size_t)b.total_px * 4));
     CK(ctx->pix2.ensure((size_t)b.total_px * 4));
     CK(ctx->gpart.ensure((size_t)(kGradGroups + 1) * M * 4));
-    CKS(power_iteration(ctx, (int64_t)K * M, kTagLd,
-                        [&](const float *u, float *w) { return apply_ztz(ctx, z_dev, u, w); }, 1,
-                        nullptr, 0.0));
+    CKS(build_sparse(ctx, z_dev));
+    scsc_status stt = power_iteration(
+        ctx, (int64_t)K * M, kTagLd,
+        [&](const float *u, float *w) { return apply_ztz(ctx, z_dev, u, w); }, 1, nullptr, 0.0);
+    ctx->sp_use = false;
+    CKS(stt);
     // r = D z - x, then the blocks in order; the residual follows each block
     CK(launch_synth_fp32(b, K, s, d_dev, z_dev, nullptr, x_dev, ctx->r.as<float>(), st));
     float *partial = ctx->gpart.as<float>(), *delta = partial + (size_t)kGradGroups * M;

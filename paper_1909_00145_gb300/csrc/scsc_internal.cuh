@@ -87,6 +87,26 @@ cudaError_t launch_filter_grad_fp32(const BatchDev &b, int K, int s, const float
                                     int n_groups, cudaStream_t st);
 cudaError_t launch_reduce_partials(const float *partial, int n_groups, int len, double *out,
                                    cudaStream_t st);
+// The dictionary step's code operators on the nonzero codes (kernels_sparse.cu):
+// count per pixel and per (filter, 128-pixel tile), exclusive scans into int64
+// offsets (scratch: sparse_scan_scratch(n) int64), the pixel-major and
+// filter-major entries, the gathered synthesis (minus x when given) and the
+// filter gradient as `groups` partials [groups][K][s*s].
+int sparse_tiles(int64_t total_px);
+size_t sparse_scan_scratch(int64_t n);
+cudaError_t launch_sparse_count(const BatchDev &b, int K, const float *z, int *cnt_px,
+                                int *cnt_kt, cudaStream_t st);
+cudaError_t launch_scan_counts(const int *in, int64_t n, int64_t *out, int64_t *scratch,
+                               cudaStream_t st);
+cudaError_t launch_sparse_fill(const BatchDev &b, int K, const float *z, const int64_t *row_ptr,
+                               const int64_t *kt_off, int *pk, float *pv, int *kpix, int *kimg,
+                               float *kv, cudaStream_t st);
+cudaError_t launch_sparse_synth(const BatchDev &b, int K, int s, const float *d,
+                                const int64_t *row_ptr, const int *pk, const float *pv,
+                                const float *x, float *out, cudaStream_t st);
+cudaError_t launch_sparse_grad(const BatchDev &b, int K, int s, const float *r,
+                               const int64_t *kt_off, const int *kpix, const int *kimg,
+                               const float *kv, float *partial, int groups, cudaStream_t st);
 cudaError_t launch_sum_sq_abs(const float *a, int64_t n_sq, const float *b, int64_t n_abs,
                               double *partials, int n_blocks, cudaStream_t st);
 cudaError_t launch_finish_sum(const double *partials, int n_blocks, double scale_sq,

@@ -248,9 +248,13 @@ def test_code_step_fixed_step(prec):
 
 # ------------------------------------------------------------------ dictionary steps
 
-def test_dict_step_batch_fp32():
+@pytest.mark.parametrize("density", [0.05, 0.002, 0.1])
+def test_dict_step_batch_fp32(density):
+    """Eq. 5 against the oracle.  Codes sparser than 1/16 run the operators
+    on the nonzero codes only (0.05, 0.002); denser ones the dense operators
+    (0.1)."""
     K, s, H, W = 12, 11, [40, 33], [50, 61]
-    x, d, z = make_case(H, W, K, s, seed=6, code_density=0.05)
+    x, d, z = make_case(H, W, K, s, seed=6, code_density=density)
     cfg = R.Config(K=K, s=s, seed=77)
     rb = R.Batch(H=H, W=W, ids=[0, 1])
     do = R.dict_step_batch(cfg, rb, x, z, d)
@@ -347,12 +351,16 @@ def test_code_step_many_items_per_cta(prec):
         check_bf16_codes(zg, zo)
 
 
-@pytest.mark.parametrize("K,s,H,W", [(12, 11, [40, 33], [50, 61]), (20, 5, [37, 64], [131, 64]),
-                                     (5, 3, [9], [12])])
-def test_dict_step_gauss_seidel_fp32(K, s, H, W):
+@pytest.mark.parametrize("K,s,H,W,density", [(12, 11, [40, 33], [50, 61], 0.08),
+                                             (20, 5, [37, 64], [131, 64], 0.08),
+                                             (5, 3, [9], [12], 0.08),
+                                             (20, 7, [37, 64], [131, 64], 0.01)])
+def test_dict_step_gauss_seidel_fp32(K, s, H, W, density):
     """One Gauss-Seidel pass of projected block coordinate descent (Sec. 3.2)
-    against the oracle: every block sees the residual of the blocks before."""
-    x, d, z = make_case(H, W, K, s, seed=16, code_density=0.08)
+    against the oracle: every block sees the residual of the blocks before.
+    At density 0.01 the step size comes from the operators on the nonzero
+    codes."""
+    x, d, z = make_case(H, W, K, s, seed=16, code_density=density)
     ids = list(range(len(H)))
     cfg = R.Config(K=K, s=s, seed=71)
     rb = R.Batch(H=H, W=W, ids=ids)
