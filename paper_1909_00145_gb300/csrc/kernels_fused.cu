@@ -38,7 +38,7 @@
 //           warp shuffles (warp-edge halo through shared memory), written for
 //           the owned rows; the block is zeroed for reuse.
 //   16      copies (lane 0): packed values and indices of each item in
-//           chunks of 2048 into a ring of staging buffers by bulk copy, and
+//           chunks of up to 4096 into a ring of staging buffers by bulk copy, and
 //           the updated values of owned items back to the output array.
 // Every wait is bounded; on timeout the CTA raises an abort flag, every role
 // leaves its loop, the copies and MMAs in flight are waited for (bounded) and
@@ -69,7 +69,7 @@ struct Fus {
   static constexpr int kFoldW = 4;
   static constexpr int kRB = 16;          // synthesis ring blocks of 16 TMEM columns
   static_assert(S <= kRB, "synthesis ring too small");
-  static constexpr int kCH = 2048;        // packed values per staging chunk
+  static constexpr int kCH = 4096;        // packed values per staging chunk (one item at p = 1/4, K <= 112)
   static constexpr int W_PROD0 = 1, W_EPI0 = 4, W_FOLD0 = 12, W_COPY = 16;
   static constexpr int kThreads = 32 * 17;
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)S * Kp * 32; }
@@ -478,8 +478,12 @@ __global__ void __launch_bounds__(Fus<S>::kThreads, 1) fused_kernel(const FusedA
     const float alpha = iterate ? A.prm->alpha : 0.0f, thr = iterate ? A.prm->thresh : 0.0f;
     const uint32_t g_base = tc::smem_u32(Gs), a_base = tc::smem_u32(As);
     const uint32_t lane_base = taddr + ((uint32_t)(32 * quarter) << 16);
-    // this thread's pixel row inside a core matrix (G in the A-tile layout, FP32)
-    const uint32_t g_row = g_base + 4u * (uint32_t)((p >> 3) * 64 + (p & 7) * 8);
+    // this thread's pixel row inside a core matrix (G in the A-tile layout,
+    // FP32); the two 16-byte halves of the 32-byte row are swapped for pixels
+    // with bit 2 set, so that the 16-byte stores of 8 consecutive pixels fall
+    // in different bank groups (element e at byte 4e ^ ((e >> 1) & 16))
+    const uint32_t g_row = 4u * (uint32_t)((p >> 3) * 64 + (p & 7) * 8);
+    const uint32_t g_sw = (uint32_t)((p >> 2) & 1) << 4;
     const int cols = Kp / 2, c0 = half * cols;  // this warp's accumulator columns
     const uint32_t e_max = (uint32_t)(kStrip * Kp);  // elements of G and of an A tile
     ChunkIter<kCH> ci;
@@ -527,11 +531,12 @@ __global__ void __launch_bounds__(Fus<S>::kThreads, 1) fused_kernel(const FusedA
               for (int j = 0; j < 4; ++j) {
                 if (j < n8) {
                   const int k = c0 + k0 + 8 * j;
-                  const uint32_t sa = g_row + 4u * (uint32_t)((k >> 3) * 1024);
+                  const uint32_t so = g_row + 4u * (uint32_t)((k >> 3) * 1024);
+                  const uint32_t sa = g_base + (so ^ g_sw), sb = g_base + ((so + 16) ^ g_sw);
                   asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(sa), "r"(r[8 * j]),
                                "r"(r[8 * j + 1]), "r"(r[8 * j + 2]), "r"(r[8 * j + 3])
                                : "memory");
-                  asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(sa + 16),
+                  asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(sb),
                                "r"(r[8 * j + 4]), "r"(r[8 * j + 5]), "r"(r[8 * j + 6]),
                                "r"(r[8 * j + 7])
                                : "memory");
@@ -588,8 +593,10 @@ __global__ void __launch_bounds__(Fus<S>::kThreads, 1) fused_kernel(const FusedA
               const uint32_t e_lo = iw[h] & 0xFFFFu, e_hi = iw[h] >> 16;
               const bool in_lo = e_lo < e_max, in_hi = e_hi < e_max;
               if (iterate) {
-                const float g_lo = in_lo ? tc::ld_shared(g_base + 4u * e_lo) : 0.0f;
-                const float g_hi = in_hi ? tc::ld_shared(g_base + 4u * e_hi) : 0.0f;
+                const float g_lo =
+                    in_lo ? tc::ld_shared(g_base + ((4u * e_lo) ^ ((e_lo >> 1) & 16u))) : 0.0f;
+                const float g_hi =
+                    in_hi ? tc::ld_shared(g_base + ((4u * e_hi) ^ ((e_hi >> 1) & 16u))) : 0.0f;
                 const float v0 = bf16_lo(vw[h]) - alpha * g_lo;
                 const float v1 = bf16_hi(vw[h]) - alpha * g_hi;
                 vw[h] = pack_bf16x2(v0 - fminf(fmaxf(v0, -thr), thr),
