@@ -1100,7 +1100,8 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   }
   // the fused kernel (BF16 packed codes) where it fits, else the two-kernel
   // paths (FP32 packed codes)
-  const int fused_ncb = ws.fused ? fused_chunk_buffers(K, s, ws.max_smem) : 0;
+  const bool fused_fits_p = ws.sample_p * kStrip * K <= 4096.0;
+  const int fused_ncb = ws.fused && fused_fits_p ? fused_chunk_buffers(K, s, ws.max_smem) : 0;
   const bool use_fused = fused_ncb > 0;
   // filter operand images, sampled-code layout, warm start
   prep_filters_kernel<<<64, 256, 0, st>>>(d, K, s, Kp, as<__nv_bfloat16>(ws.badj),

@@ -646,6 +646,7 @@ static scsc_status code_step_impl(scsc_ctx *ctx, const scsc_batch *batch, const 
     int *nf = nonfinite_word(ctx);
     if (!nf) return fail(ctx, SCSC_ENOMEM, "input check: flag allocation failed");
     CK(cudaMemsetAsync(errw, 0, sizeof(int), st));
+    ctx->tc.sample_p = (double)ctx->cfg.p_num / (double)ctx->cfg.p_den;
     cudaError_t e = tc_code_step(ctx->tc, b, batch->H, batch->W, K, s, x_dev, d_dev, z_dev,
                                  bits, obs, prm, n_iters, keep, nf, st);
     if (e == cudaErrorNotSupported)

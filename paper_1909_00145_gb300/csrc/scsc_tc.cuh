@@ -57,6 +57,12 @@ struct TcWorkspace {
   int max_smem = 0;
   Profiler *prof = nullptr;  // the owning context's profiler
   bool autotune = true, graphs = true, fused = true;
+  // sampling rate p of the code step (set by the caller before each call):
+  // the fused kernel is chosen only while an item's expected sampled codes,
+  // 128 K p, fit one of its staging chunks (4096 values); at higher p the
+  // two-kernel path is the faster one (C3 at p = 1/4: 632 vs 509
+  // Gpix*filter/s; inpainting at p = 1: 141 vs 277)
+  double sample_p = 1.0;
   std::map<TuneKey, int> tune;                       // chosen variant per key
   std::map<TuneKey, std::pair<float, float>> tune_ms;  // timings that chose it
   GraphSlot graphs_cached[kGraphSlots];

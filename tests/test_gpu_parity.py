@@ -167,10 +167,11 @@ def test_mma_rate_is_plausible(layout):
 
 # ------------------------------------------------------------------ code step
 
-def run_code_step(prec, K, s, H, W, p, n_iters, t=1, seed=0, lam=1.0, warm=None, step=0.0):
+def run_code_step(prec, K, s, H, W, p, n_iters, t=1, seed=0, lam=1.0, warm=None, step=0.0,
+                  flags=0):
     x, d, _ = make_case(H, W, K, s, seed=seed)
     z0 = np.zeros(int(np.sum(np.multiply(H, W))) * K, dtype=np.float32) if warm is None else warm
-    ctx = scsc.Context(K, s, lam=lam, p=p, seed=seed + 100, prec=prec, step=step)
+    ctx = scsc.Context(K, s, lam=lam, p=p, seed=seed + 100, prec=prec, step=step, flags=flags)
     b = scsc.Batch(H, W, ids=list(range(10, 10 + len(H))))
     zt = dev(z0)
     ctx.code_step(b, dev(x), dev(d), zt, t, n_iters)
@@ -210,6 +211,20 @@ def test_code_step_ragged_batch(prec):
         assert rel_l2(zg, zo) < 1e-4
     else:
         check_bf16_codes(zg, zo)
+
+
+@pytest.mark.parametrize("flags", [0, scsc.SCSC_FLAG_TWO_KERNEL])
+def test_code_step_both_tensor_paths(flags):
+    """The one-launch fused kernel (BF16 packed codes; chosen while an item's
+    128 K p sampled codes fit one staging chunk) and the two-kernel path (FP32
+    packed codes), on the same ragged batch, against the oracle."""
+    H, W = [37, 20, 64], [131, 260, 64]
+    zg, zo, fg, fo, _ = run_code_step("bf16", 24, 11, H, W, (1, 3), 10, seed=5, lam=0.7,
+                                      flags=flags)
+    measured(f"paths_{flags}", rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo),
+             obj=abs(fg - fo) / abs(fo))
+    assert fg == pytest.approx(fo, rel=1e-3)
+    check_bf16_codes(zg, zo)
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
