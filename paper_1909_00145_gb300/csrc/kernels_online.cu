@@ -124,6 +124,54 @@ __global__ void symv_kernel(const float *__restrict__ Cm, int64_t n, const float
   }
 }
 
+// The same update from the index of the nonzero codes (kernels_sparse.cu):
+// one warp per row a = (k, u, v) of C.  Row a of Z^T Z collects, for every
+// nonzero z_k(q1), the pixel q = q1 - c + (u, v) whose patch holds it in
+// column a, times every nonzero of q's patch: z_k2(q2) with q2 in the s x s
+// window of q lands in column (k2, u2, v2), (u2, v2) = q + c - q2.  The row
+// is decayed first; the lanes then split each patch's window, whose nonzeros
+// fall in distinct columns, and a warp barrier orders one patch's updates
+// before the next's, so the sums are deterministic.  B[a] accumulates
+// z_k(q1) x(q) in FP64 on lane 0.
+__global__ void __launch_bounds__(256) surrogate_sparse_kernel(
+    BatchDev b, int K, int S, const float *__restrict__ x, const int64_t *__restrict__ row_ptr,
+    const int *__restrict__ pk, const float *__restrict__ pv, const int64_t *__restrict__ kt_off,
+    int ntiles, const int *__restrict__ kpix, const int *__restrict__ kimg,
+    const float *__restrict__ kv, int KM, float alpha, float beta, float *__restrict__ Cm,
+    double *__restrict__ Bv) {
+  const int64_t a = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (a >= KM) return;
+  const int M = S * S, C = (S - 1) / 2;
+  const int k = (int)(a / M), m = (int)(a - (int64_t)k * M), u = m / S, v = m - (m / S) * S;
+  float *const crow = Cm + a * KM;
+  if (alpha != 1.0f)
+    for (int64_t j = lane; j < KM; j += 32) crow[j] *= alpha;
+  __syncwarp();
+  double bsum = 0.0;
+  const int64_t kb = kt_off[(int64_t)k * ntiles], ke = kt_off[(int64_t)(k + 1) * ntiles];
+  for (int64_t e = kb; e < ke; ++e) {
+    const int n = kimg[e];
+    const int H = b.H[n], W = b.W[n];
+    const int64_t base = b.off[n];
+    const int local = (int)(kpix[e] - base);
+    const int y = local / W - C + u, xx = local - (local / W) * W - C + v;
+    if (y < 0 || y >= H || xx < 0 || xx >= W) continue;  // the same on every lane
+    const float z1 = kv[e];
+    if (lane == 0) bsum += (double)z1 * (double)x[base + (int64_t)y * W + xx];
+    for (int wi = lane; wi < M; wi += 32) {
+      const int u2 = wi / S, v2 = wi - (wi / S) * S;
+      const int y2 = y + C - u2, x2 = xx + C - v2;
+      if (y2 < 0 || y2 >= H || x2 < 0 || x2 >= W) continue;
+      const int64_t g2 = base + (int64_t)y2 * W + x2;
+      for (int64_t e2 = row_ptr[g2]; e2 < row_ptr[g2 + 1]; ++e2)
+        crow[(int64_t)pk[e2] * M + wi] += beta * z1 * pv[e2];
+    }
+    __syncwarp();
+  }
+  if (lane == 0) Bv[a] = (double)alpha * Bv[a] + (double)beta * bsum;
+}
+
 __global__ void double_to_float_kernel(const double *in, float *out, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (float)in[i];
@@ -145,6 +193,19 @@ cudaError_t launch_surrogate_update(const BatchDev &b, int K, int s, const float
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   surrogate_b_kernel<<<KM, 256, 0, st>>>(b, K, s, z, x, KM, alpha, beta, Bv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, const float *x,
+                                           const int64_t *row_ptr, const int *pk, const float *pv,
+                                           const int64_t *kt_off, const int *kpix,
+                                           const int *kimg, const float *kv, double alpha,
+                                           double beta, float *Cm, double *Bv, cudaStream_t st) {
+  const int KM = K * s * s;
+  const int64_t blocks = ((int64_t)KM + 7) / 8;
+  surrogate_sparse_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+      b, K, s, x, row_ptr, pk, pv, kt_off, sparse_tiles(b.total_px), kpix, kimg, kv, KM,
+      (float)alpha, (float)beta, Cm, Bv);
   return cudaGetLastError();
 }
 

@@ -1108,9 +1108,20 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
     CK(cudaMemsetAsync(ctx->C.p, 0, (size_t)KM * KM * 4, st));
     CK(cudaMemsetAsync(ctx->B.p, 0, (size_t)KM * 8, st));
   }
-  cudaError_t e = launch_surrogate_update(b, K, s, z_dev, x_dev, (double)(t - 1) / (double)t,
-                                          1.0 / ((double)t * b.n), ctx->C.as<float>(),
-                                          ctx->B.as<double>(), st);
+  // on the nonzero codes where they are sparse enough, else the dense
+  // implicit GEMM over every pixel
+  CKS(build_sparse(ctx, z_dev));
+  const double decay = (double)(t - 1) / (double)t, w_new = 1.0 / ((double)t * b.n);
+  cudaError_t e =
+      ctx->sp_use
+          ? launch_surrogate_update_sparse(
+                b, K, s, x_dev, ctx->sp_row.as<int64_t>(), ctx->sp_pk.as<int>(),
+                ctx->sp_pv.as<float>(), ctx->sp_kt.as<int64_t>(), ctx->sp_kpix.as<int>(),
+                ctx->sp_kimg.as<int>(), ctx->sp_kv.as<float>(), decay, w_new, ctx->C.as<float>(),
+                ctx->B.as<double>(), st)
+          : launch_surrogate_update(b, K, s, z_dev, x_dev, decay, w_new, ctx->C.as<float>(),
+                                    ctx->B.as<double>(), st);
+  ctx->sp_use = false;
   CK(e);
   CKS(power_iteration(ctx, KM, kTagLc,
                       [&](const float *u, float *w) -> scsc_status {

@@ -109,6 +109,13 @@ bool tc_pipe_supported(int K, int s, int max_smem);
 cudaError_t launch_surrogate_update(const BatchDev &b, int K, int s, const float *z, const float *x,
                                     double alpha, double beta, float *Cm, double *Bv,
                                     cudaStream_t st);
+// The same update from the index of the nonzero codes (dictionary-step index
+// of kernels_sparse.cu), O(nnz * patch nonzeros) instead of O(D (K s^2)^2).
+cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, const float *x,
+                                           const int64_t *row_ptr, const int *pk, const float *pv,
+                                           const int64_t *kt_off, const int *kpix,
+                                           const int *kimg, const float *kv, double alpha,
+                                           double beta, float *Cm, double *Bv, cudaStream_t st);
 cudaError_t launch_symv(const float *Cm, int64_t n, const float *v, const double *unused,
                         float *out, cudaStream_t st);
 cudaError_t launch_symv_grad(const float *Cm, int64_t n, const float *d, const double *Bv,

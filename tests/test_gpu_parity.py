@@ -332,6 +332,30 @@ def test_dict_step_online_k64_s11():
     assert np.all(np.linalg.norm(host(dt).reshape(K, -1), axis=1) <= 1 + 1e-6)
 
 
+@pytest.mark.parametrize("K,s,density", [(400, 3, 0.01), (48, 7, 0.02), (48, 7, 0.1)])
+def test_dict_step_online_surrogate_paths(K, s, density):
+    """Eq. 7-8 over three streamed mini-batches against the oracle.  Codes
+    sparser than 1/16 update the surrogates from the nonzero codes only (K =
+    400, the filter count of the paper's large online runs, at s = 3; K = 48 at
+    s = 7); denser ones through the dense implicit GEMM (density 0.1)."""
+    H, W = [16, 12], [20, 18]
+    cfg = R.Config(K=K, s=s, seed=13)
+    st = R.OnlineState(cfg)
+    ctx = scsc.Context(K, s, seed=13)
+    b = scsc.Batch(H, W)
+    rb = R.Batch(H=H, W=W, ids=[0, 1])
+    _, d, _ = make_case(H, W, K, s, seed=51)
+    dt = dev(d)
+    d_o = d.astype(np.float64).ravel()
+    for t in range(1, 4):
+        x, _, z = make_case(H, W, K, s, seed=60 + t, code_density=density)
+        st.update(rb, x, z)
+        d_o = st.dict_step(d_o)
+        ctx.dict_step(b, dev(x), dev(z), dt, scsc.SCSC_DICT_ONLINE, t)
+        measured(f"online_{K}_{s}_{density}_t{t}", rel=rel_l2(host(dt), d_o))
+        assert rel_l2(host(dt), d_o) < 1e-5
+
+
 def test_code_step_bf16_large_k_fallback_kernels():
     """128 < K <= 256 runs the single-stage tensor kernels."""
     zg, zo, fg, fo, _ = run_code_step("bf16", 150, 5, [20, 9], [70, 140], (1, 4), 6, seed=4, lam=0.6)
