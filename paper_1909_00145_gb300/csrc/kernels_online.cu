@@ -105,7 +105,10 @@ __global__ void surrogate_b_kernel(BatchDev b, int K, int S, const float *__rest
   if (threadIdx.x == 0) Bv[col] = alpha * Bv[col] + beta * red[0];
 }
 
-// out[a] = sum_b C[a][b] v[b] (- Bv[a]), one warp per row, FP64 accumulation.
+// out[a] = sum_b C[a][b] v[b] (- Bv[a]), one warp per row.  Each lane keeps
+// four FP32 partial sums over runs of 128 products (FP32 FMAs: this GPU's FP64
+// rate would make the product FMA-bound instead of bandwidth-bound) and folds
+// each run into an FP64 total, which the warp reduces in FP64.
 template <bool kGrad>
 __global__ void symv_kernel(const float *__restrict__ Cm, int64_t n, const float *__restrict__ v,
                             const double *__restrict__ Bv, float *__restrict__ outf,
@@ -115,7 +118,13 @@ __global__ void symv_kernel(const float *__restrict__ Cm, int64_t n, const float
   if (row >= n) return;
   const float *cr = Cm + row * n;
   double s = 0.0;
-  for (int64_t j = lane; j < n; j += 32) s += (double)cr[j] * (double)v[j];
+  for (int64_t j0 = 0; j0 < n; j0 += 32 * 128) {
+    float p[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int64_t j1 = j0 + 32 * 128 < n ? j0 + 32 * 128 : n;
+#pragma unroll 4
+    for (int64_t j = j0 + lane; j < j1; j += 32) p[(j >> 5) & 3] = fmaf(cr[j], v[j], p[(j >> 5) & 3]);
+    s += ((double)p[0] + (double)p[1]) + ((double)p[2] + (double)p[3]);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) {
@@ -159,14 +168,28 @@ __global__ void __launch_bounds__(256) surrogate_sparse_kernel(
     if (y < 0 || y >= H || xx < 0 || xx >= W) continue;  // the same on every lane
     const float z1 = kv[e];
     if (lane == 0) bsum += (double)z1 * (double)x[base + (int64_t)y * W + xx];
-    for (int wi = lane; wi < M; wi += 32) {
-      const int u2 = wi / S, v2 = wi - (wi / S) * S;
-      const int y2 = y + C - u2, x2 = xx + C - v2;
-      if (y2 < 0 || y2 >= H || x2 < 0 || x2 >= W) continue;
-      const int64_t g2 = base + (int64_t)y2 * W + x2;
-      for (int64_t e2 = row_ptr[g2]; e2 < row_ptr[g2 + 1]; ++e2)
-        crow[(int64_t)pk[e2] * M + wi] += beta * z1 * pv[e2];
+    // the window's offsets first (up to 4 pixels per lane, s <= 11), so that
+    // their loads are in flight together
+    int64_t rb[4], re[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int wi = lane + 32 * r;
+      rb[r] = re[r] = 0;
+      if (wi < M) {
+        const int u2 = wi / S, v2 = wi - (wi / S) * S;
+        const int y2 = y + C - u2, x2 = xx + C - v2;
+        if (y2 >= 0 && y2 < H && x2 >= 0 && x2 < W) {
+          const int64_t g2 = base + (int64_t)y2 * W + x2;
+          rb[r] = row_ptr[g2];
+          re[r] = row_ptr[g2 + 1];
+        }
+      }
     }
+    const float bz = beta * z1;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      for (int64_t e2 = rb[r]; e2 < re[r]; ++e2)
+        crow[(int64_t)pk[e2] * M + lane + 32 * r] += bz * pv[e2];
     __syncwarp();
   }
   if (lane == 0) Bv[a] = (double)alpha * Bv[a] + (double)beta * bsum;
