@@ -134,7 +134,8 @@ __global__ void symv_kernel(const float *__restrict__ Cm, int64_t n, const float
 }
 
 // The same update from the index of the nonzero codes (kernels_sparse.cu):
-// one warp per row a = (k, u, v) of C.  Row a of Z^T Z collects, for every
+// one warp per row a = (k, u, v) of C, over the columns of filters k2 >= k
+// only (C is symmetric; mirror_lower_kernel copies the rest).  Row a of Z^T Z collects, for every
 // nonzero z_k(q1), the pixel q = q1 - c + (u, v) whose patch holds it in
 // column a, times every nonzero of q's patch: z_k2(q2) with q2 in the s x s
 // window of q lands in column (k2, u2, v2), (u2, v2) = q + c - q2.  The row
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(256) surrogate_sparse_kernel(
   const int k = (int)(a / M), m = (int)(a - (int64_t)k * M), u = m / S, v = m - (m / S) * S;
   float *const crow = Cm + a * KM;
   if (alpha != 1.0f)
-    for (int64_t j = lane; j < KM; j += 32) crow[j] *= alpha;
+    for (int64_t j = (int64_t)k * M + lane; j < KM; j += 32) crow[j] *= alpha;
   __syncwarp();
   double bsum = 0.0;
   const int64_t kb = kt_off[(int64_t)k * ntiles], ke = kt_off[(int64_t)(k + 1) * ntiles];
@@ -188,11 +189,34 @@ __global__ void __launch_bounds__(256) surrogate_sparse_kernel(
     const float bz = beta * z1;
 #pragma unroll
     for (int r = 0; r < 4; ++r)
-      for (int64_t e2 = rb[r]; e2 < re[r]; ++e2)
-        crow[(int64_t)pk[e2] * M + lane + 32 * r] += bz * pv[e2];
+      for (int64_t e2 = rb[r]; e2 < re[r]; ++e2) {
+        const int k2 = pk[e2];
+        if (k2 >= k) crow[(int64_t)k2 * M + lane + 32 * r] += bz * pv[e2];
+      }
     __syncwarp();
   }
   if (lane == 0) Bv[a] = (double)alpha * Bv[a] + (double)beta * bsum;
+}
+
+// C[j][i] = C[i][j] for the columns j of filters below row i's filter: the
+// lower block triangle from the upper one, by 32 x 32 tiles through shared
+// memory (tile (bi, bj) with bj < bi reads the transposed tile (bj, bi)).
+__global__ void __launch_bounds__(256) mirror_lower_kernel(float *__restrict__ Cm, int KM, int M) {
+  __shared__ float t[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  // source: rows bj*32.., columns bi*32.. (upper), destination: rows bi*32.., columns bj*32..
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t row = (int64_t)bj * 32 + r, col = (int64_t)bi * 32 + tx;
+    t[r][tx] = (row < KM && col < KM) ? Cm[row * KM + col] : 0.0f;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t row = (int64_t)bi * 32 + r, col = (int64_t)bj * 32 + tx;
+    // only entries whose column's filter is below the row's filter
+    if (row < KM && col < KM && col / M < row / M) Cm[row * KM + col] = t[tx][r];
+  }
 }
 
 __global__ void double_to_float_kernel(const double *in, float *out, int n) {
@@ -229,6 +253,10 @@ cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, cons
   surrogate_sparse_kernel<<<(unsigned)blocks, 256, 0, st>>>(
       b, K, s, x, row_ptr, pk, pv, kt_off, sparse_tiles(b.total_px), kpix, kimg, kv, KM,
       (float)alpha, (float)beta, Cm, Bv);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int nt = (KM + 31) / 32;
+  mirror_lower_kernel<<<dim3(nt, nt), 256, 0, st>>>(Cm, KM, s * s);
   return cudaGetLastError();
 }
 
