@@ -148,7 +148,7 @@ scsc_status scsc_code_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
 /* scsc_code_step on HOST buffers: x_host (packed images), d_host (K x s x s)
  * and z_host (warm start in, Eq. 4 codes out), all float32 in scsc_code_step's
  * layouts.  The step size is taken once for the whole batch; the images are
- * then processed in up to 4 contiguous chunks (at least 2^20 pixels each), and
+ * then processed in up to 3 contiguous chunks (at least 2^20 pixels each), and
  * chunk c + 1's host-to-device copy and chunk c - 1's device-to-host copy run
  * on their own streams while chunk c computes.  Results equal scsc_code_step's
  * (every image's update is independent of the others).  Page-locked host

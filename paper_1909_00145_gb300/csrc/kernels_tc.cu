@@ -1099,9 +1099,14 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
     TRY(cudaDeviceGetAttribute(&ws.max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   }
   // the fused kernel (BF16 packed codes) where it fits, else the two-kernel
-  // paths (FP32 packed codes)
+  // paths (FP32 packed codes).  It also needs at least two row items per SM:
+  // each CTA recomputes the 2c rows around its range, so with fewer items the
+  // recomputation outweighs the saved launch (100 items of 100^2 at K = 16:
+  // 1.84 Gpix*filter/s fused, 2.07 on two kernels)
   const bool fused_fits_p = ws.sample_p * kStrip * K <= 4096.0;
-  const int fused_ncb = ws.fused && fused_fits_p ? fused_chunk_buffers(K, s, ws.max_smem) : 0;
+  const bool fused_fits_q = Q >= 2 * ws.sm_count;
+  const int fused_ncb =
+      ws.fused && fused_fits_p && fused_fits_q ? fused_chunk_buffers(K, s, ws.max_smem) : 0;
   const bool use_fused = fused_ncb > 0;
   // filter operand images, sampled-code layout, warm start
   prep_filters_kernel<<<64, 256, 0, st>>>(d, K, s, Kp, as<__nv_bfloat16>(ws.badj),

@@ -216,9 +216,10 @@ def test_code_step_ragged_batch(prec):
 @pytest.mark.parametrize("flags", [0, scsc.SCSC_FLAG_TWO_KERNEL])
 def test_code_step_both_tensor_paths(flags):
     """The one-launch fused kernel (BF16 packed codes; chosen while an item's
-    128 K p sampled codes fit one staging chunk) and the two-kernel path (FP32
-    packed codes), on the same ragged batch, against the oracle."""
-    H, W = [37, 20, 64], [131, 260, 64]
+    128 K p sampled codes fit one staging chunk and there are at least two row
+    items per SM) and the two-kernel path (FP32 packed codes), on the same
+    ragged batch (404 row items), against the oracle."""
+    H, W = [80, 60, 64], [200, 260, 64]
     zg, zo, fg, fo, _ = run_code_step("bf16", 24, 11, H, W, (1, 3), 10, seed=5, lam=0.7,
                                       flags=flags)
     measured(f"paths_{flags}", rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo),
