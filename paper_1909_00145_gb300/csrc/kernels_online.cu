@@ -198,6 +198,137 @@ __global__ void __launch_bounds__(256) surrogate_sparse_kernel(
   if (lane == 0) Bv[a] = (double)alpha * Bv[a] + (double)beta * bsum;
 }
 
+// Cross-correlations of the code maps for the surrogate update:
+//   T[k][k2][dy][dx] = sum over nonzeros z_k(r1) with r1 + (dy, dx) in the
+//   same image of z_k(r1) z_k2(r1 + (dy, dx)),  k2 >= k, |dy|, |dx| <= s - 1.
+// Entry ((k,u,v),(k2,u2,v2)) of sum_q Z[q]^T Z[q] is T[k][k2][u-u2][v-v2]
+// minus the products whose patch centre q = r1 - c + (u,v) lies outside the
+// image (only codes within c of the border have such q; surrogate_border_
+// kernel subtracts them).  Block k, thread = lag: each thread owns its lag's
+// entries of row block k and walks filter k's nonzeros in order, so the sums
+// are deterministic without barriers or atomics.
+__global__ void __launch_bounds__(512) surrogate_corr_kernel(
+    BatchDev b, int K, int S, const int64_t *__restrict__ row_ptr, const int *__restrict__ pk,
+    const float *__restrict__ pv, const int64_t *__restrict__ kt_off, int ntiles,
+    const int *__restrict__ kpix, const int *__restrict__ kimg, const float *__restrict__ kv,
+    float *__restrict__ T) {
+  const int k = blockIdx.x, D = 2 * S - 1, DD = D * D, t = threadIdx.x;
+  if (t >= DD) return;
+  const int dy = t / D - (S - 1), dx = t - (t / D) * D - (S - 1);
+  float *const Tk = T + (int64_t)k * K * DD;
+  for (int k2 = k; k2 < K; ++k2) Tk[(int64_t)k2 * DD + t] = 0.0f;
+  const int64_t kb = kt_off[(int64_t)k * ntiles], ke = kt_off[(int64_t)(k + 1) * ntiles];
+  for (int64_t e = kb; e < ke; ++e) {
+    const int n = kimg[e];
+    const int H = b.H[n], W = b.W[n];
+    const int64_t base = b.off[n];
+    const int local = (int)(kpix[e] - base);
+    const int y2 = local / W + dy, x2 = local - (local / W) * W + dx;
+    if (y2 < 0 || y2 >= H || x2 < 0 || x2 >= W) continue;
+    const float z1 = kv[e];
+    const int64_t g2 = base + (int64_t)y2 * W + x2;
+    for (int64_t e2 = row_ptr[g2]; e2 < row_ptr[g2 + 1]; ++e2) {
+      const int k2 = pk[e2];
+      if (k2 >= k) Tk[(int64_t)k2 * DD + t] += z1 * pv[e2];
+    }
+  }
+}
+
+// C[a][b] <- alpha C[a][b] + beta T[k][k2][u-u2][v-v2] over the columns b of
+// filters k2 >= k of row a = (k,u,v); one block per row.
+__global__ void __launch_bounds__(256) surrogate_expand_kernel(float *__restrict__ Cm,
+                                                               const float *__restrict__ T, int K,
+                                                               int S, float alpha, float beta) {
+  const int M = S * S, KM = K * M, D = 2 * S - 1, DD = D * D;
+  const int a = blockIdx.x;
+  const int k = a / M, m = a - k * M, u = m / S, v = m - (m / S) * S;
+  float *const crow = Cm + (int64_t)a * KM;
+  const float *const Tk = T + (int64_t)k * K * DD;
+  for (int bcol = k * M + threadIdx.x; bcol < KM; bcol += blockDim.x) {
+    const int k2 = bcol / M, m2 = bcol - k2 * M, u2 = m2 / S, v2 = m2 - (m2 / S) * S;
+    const int lag = (u - u2 + S - 1) * D + (v - v2 + S - 1);
+    crow[bcol] = alpha * crow[bcol] + beta * Tk[(int64_t)k2 * DD + lag];
+  }
+}
+
+// The rest of the update, one warp per row a = (k,u,v).  The lanes take
+// filter k's nonzeros z_k(r1) 32 at a time: for those whose patch centre
+// q = r1 - c + (u,v) lies inside the image, B[a] accumulates z_k(r1) x(q)
+// (FP64, per lane, then a fixed butterfly); those whose centre lies outside
+// are then taken in order by the whole warp, which subtracts the products
+// the correlation counted but no patch of the image holds (columns of
+// filters k2 >= k, lanes over the window).
+__global__ void __launch_bounds__(256) surrogate_border_kernel(
+    BatchDev b, int K, int S, const float *__restrict__ x, const int64_t *__restrict__ row_ptr,
+    const int *__restrict__ pk, const float *__restrict__ pv, const int64_t *__restrict__ kt_off,
+    int ntiles, const int *__restrict__ kpix, const int *__restrict__ kimg,
+    const float *__restrict__ kv, int KM, float alpha, float beta, float *__restrict__ Cm,
+    double *__restrict__ Bv) {
+  const int64_t a = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (a >= KM) return;  // whole warps
+  const int M = S * S, C = (S - 1) / 2;
+  const int k = (int)(a / M), m = (int)(a - (int64_t)k * M), u = m / S, v = m - (m / S) * S;
+  float *const crow = Cm + a * KM;
+  double bsum = 0.0;
+  const int64_t kb = kt_off[(int64_t)k * ntiles], ke = kt_off[(int64_t)(k + 1) * ntiles];
+  for (int64_t e0 = kb; e0 < ke; e0 += 32) {
+    const int64_t e = e0 + lane;
+    int n = 0, y = 0, xx = 0;
+    float z1 = 0.0f;
+    bool out = false;
+    if (e < ke) {
+      n = kimg[e];
+      const int H = b.H[n], W = b.W[n];
+      const int64_t base = b.off[n];
+      const int local = (int)(kpix[e] - base);
+      y = local / W - C + u;
+      xx = local - (local / W) * W - C + v;
+      z1 = kv[e];
+      if (y >= 0 && y < H && xx >= 0 && xx < W)
+        bsum += (double)z1 * (double)x[base + (int64_t)y * W + xx];
+      else
+        out = true;
+    }
+    unsigned todo = __ballot_sync(0xffffffffu, out);
+    while (todo) {
+      const int j = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const int nj = __shfl_sync(0xffffffffu, n, j);
+      const int yj = __shfl_sync(0xffffffffu, y, j), xj = __shfl_sync(0xffffffffu, xx, j);
+      const float bz = beta * __shfl_sync(0xffffffffu, z1, j);
+      const int H = b.H[nj], W = b.W[nj];
+      const int64_t base = b.off[nj];
+      // the window's offsets first (up to 4 pixels per lane, s <= 11)
+      int64_t rb[4], re[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int wi = lane + 32 * r;
+        rb[r] = re[r] = 0;
+        if (wi < M) {
+          const int u2 = wi / S, v2 = wi - (wi / S) * S;
+          const int y2 = yj + C - u2, x2 = xj + C - v2;
+          if (y2 >= 0 && y2 < H && x2 >= 0 && x2 < W) {
+            const int64_t g2 = base + (int64_t)y2 * W + x2;
+            rb[r] = row_ptr[g2];
+            re[r] = row_ptr[g2 + 1];
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        for (int64_t e2 = rb[r]; e2 < re[r]; ++e2) {
+          const int k2 = pk[e2];
+          if (k2 >= k) crow[(int64_t)k2 * M + lane + 32 * r] -= bz * pv[e2];
+        }
+      __syncwarp();
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+  if (lane == 0) Bv[a] = (double)alpha * Bv[a] + (double)beta * bsum;
+}
+
 // C[j][i] = C[i][j] for the columns j of filters below row i's filter: the
 // lower block triangle from the upper one, by 32 x 32 tiles through shared
 // memory (tile (bi, bj) with bj < bi reads the transposed tile (bj, bi)).
@@ -243,17 +374,39 @@ cudaError_t launch_surrogate_update(const BatchDev &b, int K, int s, const float
   return cudaGetLastError();
 }
 
+size_t surrogate_corr_floats(int K, int s) {
+  const size_t D = (size_t)(2 * s - 1);
+  return (size_t)K * K * D * D;
+}
+
 cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, const float *x,
                                            const int64_t *row_ptr, const int *pk, const float *pv,
                                            const int64_t *kt_off, const int *kpix,
                                            const int *kimg, const float *kv, double alpha,
-                                           double beta, float *Cm, double *Bv, cudaStream_t st) {
+                                           double beta, float *Cm, double *Bv, float *T,
+                                           cudaStream_t st) {
   const int KM = K * s * s;
-  const int64_t blocks = ((int64_t)KM + 7) / 8;
-  surrogate_sparse_kernel<<<(unsigned)blocks, 256, 0, st>>>(
-      b, K, s, x, row_ptr, pk, pv, kt_off, sparse_tiles(b.total_px), kpix, kimg, kv, KM,
-      (float)alpha, (float)beta, Cm, Bv);
-  cudaError_t e = cudaGetLastError();
+  const int nt_px = sparse_tiles(b.total_px);
+  cudaError_t e;
+  if (T != nullptr) {
+    // correlations, then C = alpha C + beta T (upper blocks), then the
+    // border corrections and B
+    surrogate_corr_kernel<<<K, 512, 0, st>>>(b, K, s, row_ptr, pk, pv, kt_off, nt_px, kpix, kimg,
+                                             kv, T);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    surrogate_expand_kernel<<<KM, 256, 0, st>>>(Cm, T, K, s, (float)alpha, (float)beta);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t blocks = ((int64_t)KM + 7) / 8;
+    surrogate_border_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+        b, K, s, x, row_ptr, pk, pv, kt_off, nt_px, kpix, kimg, kv, KM, (float)alpha,
+        (float)beta, Cm, Bv);
+  } else {
+    const int64_t blocks = ((int64_t)KM + 7) / 8;
+    surrogate_sparse_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+        b, K, s, x, row_ptr, pk, pv, kt_off, nt_px, kpix, kimg, kv, KM, (float)alpha,
+        (float)beta, Cm, Bv);
+  }
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nt = (KM + 31) / 32;
   mirror_lower_kernel<<<dim3(nt, nt), 256, 0, st>>>(Cm, KM, s * s);

@@ -104,6 +104,7 @@ struct scsc_ctx {
   // the dictionary step's index of the nonzero codes: counts, offsets,
   // pixel-major and filter-major entries (kernels_sparse.cu)
   DevBuf sp_cpx, sp_ckt, sp_row, sp_kt, sp_scan, sp_pk, sp_pv, sp_kpix, sp_kimg, sp_kv;
+  DevBuf sp_T;  // cross-correlations of the code maps (online surrogate update)
   bool sp_use = false;
   // online surrogates
   DevBuf C, B, Cd;
@@ -1115,13 +1116,18 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
   // implicit GEMM over every pixel
   CKS(build_sparse(ctx, z_dev));
   const double decay = (double)(t - 1) / (double)t, w_new = 1.0 / ((double)t * b.n);
+  float *sp_corr = nullptr;  // the correlation buffer of the sparse update
+  if (ctx->sp_use) {
+    CK(ctx->sp_T.ensure(surrogate_corr_floats(K, s) * 4));
+    sp_corr = ctx->sp_T.as<float>();
+  }
   cudaError_t e =
       ctx->sp_use
           ? launch_surrogate_update_sparse(
                 b, K, s, x_dev, ctx->sp_row.as<int64_t>(), ctx->sp_pk.as<int>(),
                 ctx->sp_pv.as<float>(), ctx->sp_kt.as<int64_t>(), ctx->sp_kpix.as<int>(),
                 ctx->sp_kimg.as<int>(), ctx->sp_kv.as<float>(), decay, w_new, ctx->C.as<float>(),
-                ctx->B.as<double>(), st)
+                ctx->B.as<double>(), sp_corr, st)
           : launch_surrogate_update(b, K, s, z_dev, x_dev, decay, w_new, ctx->C.as<float>(),
                                     ctx->B.as<double>(), st);
   ctx->sp_use = false;

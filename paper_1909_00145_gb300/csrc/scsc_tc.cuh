@@ -115,7 +115,11 @@ cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, cons
                                            const int64_t *row_ptr, const int *pk, const float *pv,
                                            const int64_t *kt_off, const int *kpix,
                                            const int *kimg, const float *kv, double alpha,
-                                           double beta, float *Cm, double *Bv, cudaStream_t st);
+                                           double beta, float *Cm, double *Bv, float *T,
+                                           cudaStream_t st);
+// Floats of the correlation buffer T of that update (K * K * (2s-1)^2); with
+// T == nullptr the update walks every patch instead (no buffer).
+size_t surrogate_corr_floats(int K, int s);
 cudaError_t launch_symv(const float *Cm, int64_t n, const float *v, const double *unused,
                         float *out, cudaStream_t st);
 cudaError_t launch_symv_grad(const float *Cm, int64_t n, const float *d, const double *Bv,
