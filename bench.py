@@ -392,21 +392,22 @@ def dict_report(steps=5):
     print(json.dumps(out), flush=True)
 
 
-def online_report(batches=4):
+def online_report(prec="bf16", batches=4):
     """The online workload of Alg. 2 at its stated size, on a prefix of the
     stream: mini-batches of eta = 50 new 100x100 images, K = 400 filters of
     11x11, p = 1/10, lambda = 1, 20 PG iterations per mini-batch, each
     followed by the online dictionary step (Eq. 7 surrogate update, Eq. 8
     projected-gradient step with its power iteration on the 48,400 x 48,400
-    surrogate).  The code step runs the plain FP32 path (the tensor path stops
-    at K = 256).  One warm-up mini-batch, then `batches` timed ones; one JSON
-    line with the code-update throughput and the dictionary step's time."""
+    surrogate).  The code step runs on `prec`: the tensor path (its
+    single-stage kernels at this K) or the plain FP32 path.  One warm-up
+    mini-batch, then `batches` timed ones; one JSON line with the code-update
+    throughput and the dictionary step's time."""
     import torch
     from paper_1909_00145_gb300 import inputs as I
     from paper_1909_00145_gb300 import scsc
     K, s, eta, side, n_iters, p = 400, 11, 50, 100, 20, (1, 10)
     stream = torch.cuda.Stream()
-    ctx = scsc.Context(K, s, 1.0, p, seed=0, prec="fp32", stream=stream)
+    ctx = scsc.Context(K, s, 1.0, p, seed=0, prec=prec, stream=stream)
     H = np.full(eta, side, dtype=np.int32)
     W = np.full(eta, side, dtype=np.int32)
     d = torch.from_numpy(I.filters(7, K, s)).cuda().contiguous()
@@ -441,7 +442,7 @@ def online_report(batches=4):
     print(json.dumps({
         "metric": "code-update Gpix*filter/s", "value": npx * K * n_iters / (cm * 1e-3) / 1e9,
         "unit": "Gpix*filter/s", "n_gpus": 1, "steps": batches, "warmup": 1,
-        "higher_is_better": True, "dtype": "fp32", "data": "synthetic",
+        "higher_is_better": True, "dtype": prec, "data": "synthetic",
         "config": {"workload": f"online (Alg. 2): mini-batches of {eta} x {side}x{side} blob images, "
                                f"K={K} {s}x{s}, p=1/10, lambda=1, {n_iters} PG its per mini-batch, "
                                "then the online dictionary step"},
@@ -474,7 +475,7 @@ def main():
                     help="time the online workload at K=400 (Alg. 2 prefix) and exit")
     args = ap.parse_args()
     if args.online:
-        online_report()
+        online_report(args.prec)
         return
     if args.accuracy:
         accuracy_report()

@@ -140,7 +140,7 @@ __global__ void scan_add_kernel(uint64_t *out, int n, const uint64_t *block_sums
 // One block per item.  The item's dense codes are one contiguous block of
 // npx * K floats, walked linearly by the block (coalesced); each element
 // finds its packed slot from per-pixel chunk offsets staged in shared memory.
-constexpr int kMaxChunks = 16;  // K <= 256
+constexpr int kMaxChunks = 32;  // K <= 512
 __global__ void __launch_bounds__(kThreads) pack_kernel(ItemMap im, int K, int KW, int NC,
                                                         const uint32_t *bits,
                                                         const uint64_t *seg_base,
@@ -338,10 +338,12 @@ template <int S>
 struct SynthSmem {
   static constexpr int C = (S - 1) / 2;
   static constexpr int N = 16 * S;
-  __host__ __device__ static size_t a_bytes(int Kp) { return (size_t)kStrip * Kp * 2; }
+  // A holds a_chunks filter chunks of 16 (4 KB each): all Kp / 16 where they
+  // fit beside B, else the chunks are built and multiplied in groups
+  __host__ __device__ static size_t a_bytes(int a_chunks) { return (size_t)a_chunks * 4096; }
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)N * Kp * 2; }
-  __host__ __device__ static size_t total(int Kp) {
-    return 1024 + a_bytes(Kp) + b_bytes(Kp) + (size_t)2 * S * kPuRow * 4;
+  __host__ __device__ static size_t total(int Kp, int a_chunks) {
+    return 1024 + a_bytes(a_chunks) + b_bytes(Kp) + (size_t)2 * S * kPuRow * 4;
   }
 };
 
@@ -353,14 +355,15 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
                                                             const float *__restrict__ packed,
                                                             const uint4 *__restrict__ bsyn,
                                                             float *__restrict__ xcore,
-                                                            float *__restrict__ spill, int *err) {
+                                                            float *__restrict__ spill,
+                                                            int a_chunks, int *err) {
   using L = SynthSmem<S>;
   constexpr int C = L::C, N = L::N;
   const int NC = Kp / 16;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *As = smem;
-  uint8_t *Bs = As + L::a_bytes(Kp);
+  uint8_t *Bs = As + L::a_bytes(a_chunks);
   float *Pu = reinterpret_cast<float *>(Bs + L::b_bytes(Kp));  // [2][S][kPuRow]
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
@@ -410,45 +413,50 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
 
     for (int a = a_start; a < a_end; ++a) {
       const int qa = it.q_row0 + a;
-      // 1. expand the packed codes of code row a (this thread: pixel i) into
-      // the A operand (BF16)
       const float *src = packed + seg_base[qa] + pxoff[(int64_t)qa * kStrip + i];
-      for (int c = 0; c < NC; ++c) {
-        const uint32_t m = chunk_mask(bits, KW, it, a, b0 + i, c);
-        float v[16];
+      for (int g0 = 0; g0 < NC; g0 += a_chunks) {
+        const int g1 = min(NC, g0 + a_chunks);
+        // 1. expand the packed codes of code row a (this thread: pixel i),
+        // filter chunks g0 .. g1-1, into the A operand (BF16)
+        for (int c = g0; c < g1; ++c) {
+          const uint32_t m = chunk_mask(bits, KW, it, a, b0 + i, c);
+          float v[16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          v[e] = ((m >> e) & 1u) ? __ldg(src) : 0.0f;
-          src += (m >> e) & 1u;
+          for (int e = 0; e < 16; ++e) {
+            v[e] = ((m >> e) & 1u) ? __ldg(src) : 0.0f;
+            src += (m >> e) & 1u;
+          }
+          uint4 lo = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+          uint4 hi = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
+                                pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
+          uint8_t *dst = As + (size_t)(2 * (c - g0)) * 2048 + (i >> 3) * 128 + (i & 7) * 16;
+          *reinterpret_cast<uint4 *>(dst) = lo;
+          *reinterpret_cast<uint4 *>(dst + 2048) = hi;
         }
-        uint4 lo = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
-                              pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-        uint4 hi = make_uint4(pack_bf16x2(v[8], v[9]), pack_bf16x2(v[10], v[11]),
-                              pack_bf16x2(v[12], v[13]), pack_bf16x2(v[14], v[15]));
-        uint8_t *dst = As + (size_t)(2 * c) * 2048 + (i >> 3) * 128 + (i & 7) * 16;
-        *reinterpret_cast<uint4 *>(dst) = lo;
-        *reinterpret_cast<uint4 *>(dst + 2048) = hi;
-      }
-      tc::fence_proxy_async();
-      __syncthreads();
-      // 2. P = Z_row * D^T over all filter chunks
-      if (tid == 0) {
+        tc::fence_proxy_async();
+        __syncthreads();
+        // 2. P += Z_row * D^T over these filter chunks; the wait also frees A
+        // for the next group
+        if (tid == 0) {
+          tc::fence_after_sync();
+          for (int kk = g0; kk < g1; ++kk) {
+            uint64_t ad = tc::smem_desc(a_base + (kk - g0) * 2 * 2048, 2048, 128);
+            uint64_t bd = tc::smem_desc(b_base + kk * 2 * b_lbo, b_lbo, 128);
+            tc::mma_bf16(taddr, ad, bd, idesc, kk > 0 ? 1u : 0u);
+          }
+          tc::mma_commit(&mbar);
+        }
+        bool ok = tc::mbar_wait_bounded(&mbar, phase, kWaitNs);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+          if (tid == 0) atomicExch(err, 1);
+          failed = true;
+          break;
+        }
         tc::fence_after_sync();
-        for (int kk = 0; kk < NC; ++kk) {
-          uint64_t ad = tc::smem_desc(a_base + kk * 2 * 2048, 2048, 128);
-          uint64_t bd = tc::smem_desc(b_base + kk * 2 * b_lbo, b_lbo, 128);
-          tc::mma_bf16(taddr, ad, bd, idesc, kk > 0 ? 1u : 0u);
-        }
-        tc::mma_commit(&mbar);
       }
-      bool ok = tc::mbar_wait_bounded(&mbar, phase, kWaitNs);
-      phase ^= 1u;
-      if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicExch(err, 1);
-        failed = true;
-        break;
-      }
-      tc::fence_after_sync();
+      if (failed) break;
       // 3. col2im: output row a-c+u gets sum_v P[b + c - v][(u, v)]
 #pragma unroll
       for (int u = 0; u < S; ++u) {
@@ -605,7 +613,11 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
   tc::fence_after_sync();
   const uint32_t taddr = tmem_base;
   const uint32_t lane_addr = taddr + ((uint32_t)(32 * warp) << 16);
-  const uint32_t idesc = tc::idesc_bf16_f32(128, Kp);
+  // N <= 256 per MMA: above that the filters go in two column ranges of the
+  // accumulator, [0, n1) and [n1, Kp)
+  const int n1 = Kp <= 256 ? Kp : (Kp / 2 + 15) / 16 * 16;
+  const uint32_t idesc = tc::idesc_bf16_f32(128, n1);
+  const uint32_t idesc2 = tc::idesc_bf16_f32(128, Kp > n1 ? Kp - n1 : 16);
   const uint32_t ring_base = tc::smem_u32(ring), b_base = tc::smem_u32(Bs);
   const float alpha = prm->alpha, thr = prm->thresh;
   uint32_t phase = 0;
@@ -657,6 +669,11 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
           uint64_t ad = tc::smem_desc(ring_base + slot, 128, 128);
           uint64_t bd = tc::smem_desc(b_base + u * Kp * 32, Kp * 16, 128);
           tc::mma_bf16(taddr, ad, bd, idesc, u > 0 ? 1u : 0u);
+          if (Kp > n1) {
+            // filters n1 .. Kp-1 start n1 / 8 core groups (128 bytes each) in
+            bd = tc::smem_desc(b_base + u * Kp * 32 + n1 * 16, Kp * 16, 128);
+            tc::mma_bf16(taddr + (uint32_t)n1, ad, bd, idesc2, u > 0 ? 1u : 0u);
+          }
         }
         tc::mma_commit(&mbar);
       }
@@ -1044,8 +1061,8 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
                          int K, int s, const float *x, const float *d, float *z,
                          const uint32_t *bits, const uint8_t *obs, const StepParams *prm,
                          int n_iters, bool keep_unsampled, int *nonfinite, cudaStream_t st) {
-  if (K > 256) {
-    ws.last_error = "the tensor path supports K <= 256";
+  if (K > kMaxChunks * 16) {
+    ws.last_error = "the tensor path supports K <= 512";
     return cudaErrorNotSupported;
   }
   const int Kp = (K + 15) / 16 * 16, NC = Kp / 16, KW = (K + 31) / 32, C = (s - 1) / 2;
@@ -1137,12 +1154,23 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   const bool pipe_ok = tc_pipe_supported(K, s, ws.max_smem);
   const int fin_grid = std::min(Q, ws.sm_count * 16);  // finalize: blocks over row items
   // launch geometry of the single-stage kernels (several CTAs per SM)
-  int grid_s1 = 1, grid_a1 = 1;
+  int grid_s1 = 1, grid_a1 = 1, a_chunks = NC;
   size_t smem_s1 = 0, smem_a1 = 0;
   TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
-    smem_s1 = SynthSmem<S>::total(Kp);
+    // the synthesis keeps every filter chunk of a code row in shared memory
+    // where they fit beside the filters (1 KB left for static shared memory)
+    const size_t smem_cap = (size_t)ws.max_smem - 1024;
+    if (SynthSmem<S>::total(Kp, NC) > smem_cap) {
+      const size_t fixed = SynthSmem<S>::total(Kp, 0);
+      a_chunks = fixed < smem_cap ? (int)((smem_cap - fixed) / 4096) : 0;
+    }
+    smem_s1 = SynthSmem<S>::total(Kp, a_chunks);
     smem_a1 = AdjSmem<S>::total(Kp);
+    if (a_chunks < 1 || smem_a1 > smem_cap) {
+      ws.last_error = "the filters do not fit in shared memory";
+      return cudaErrorNotSupported;
+    }
     TRY(cudaFuncSetAttribute(synth_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_s1));
     TRY(cudaFuncSetAttribute(adj_tc_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1186,7 +1214,7 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
         constexpr int S = decltype(SC)::value;
         synth_tc_kernel<S><<<grid_s1, kThreads, smem_s1, st>>>(
             im, K, Kp, KW, bits, seg_base, pxoff, as<float>(ws.packed), as<uint4>(ws.bsyn),
-            as<float>(ws.xcore), as<float>(ws.spill), as<int>(ws.err));
+            as<float>(ws.xcore), as<float>(ws.spill), a_chunks, as<int>(ws.err));
         return cudaGetLastError();
       }));
     }

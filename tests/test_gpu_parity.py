@@ -365,6 +365,25 @@ def test_code_step_bf16_large_k_fallback_kernels():
     check_bf16_codes(zg, zo)
 
 
+@pytest.mark.parametrize("K,s,p,H,W,seed", [
+    # the online filter count at p = 1/10: the synthesis builds and multiplies
+    # its 25 filter chunks in two groups, the adjoint splits N as 208 + 192
+    (400, 11, (1, 10), [30, 24], [100, 130], 21),
+    # the largest K, every coordinate sampled: four chunk groups, N = 256 + 256,
+    # full items (the largest per-pixel offsets)
+    (512, 11, (1, 1), [14, 9], [130, 60], 22),
+    # every chunk in shared memory at s = 5, N = 160 + 144
+    (300, 5, (1, 4), [20, 9], [70, 140], 23),
+])
+def test_code_step_bf16_k_above_256(K, s, p, H, W, seed):
+    """256 < K <= 512 on the single-stage tensor kernels (Eq. 3 by PG)."""
+    zg, zo, fg, fo, _ = run_code_step("bf16", K, s, H, W, p, 5, seed=seed, lam=0.6)
+    measured(f"k_above_256_{K}", rel=rel_l2(zg, zo), jac=support_jaccard(zg, zo),
+             obj=abs(fg - fo) / abs(fo))
+    assert fg == pytest.approx(fo, rel=1e-3)
+    check_bf16_codes(zg, zo)
+
+
 @pytest.mark.parametrize("K", [128, 113, 1])
 def test_code_step_pipelined_limits(K):
     """The pipelined kernels at their limits: Kp = 128 with 11 x 11 filters and
