@@ -332,6 +332,42 @@ __global__ void __launch_bounds__(kThreads) pack16_kernel(ItemMap im, int K, int
   if (mode == 0 && __syncthreads_or(bad) && threadIdx.x == 0) atomicOr(nonfinite, 1);
 }
 
+// ------------------------------------------------------------------ row staging
+// The single-stage kernels read, per code row, every pixel's mask words and
+// the item's packed values.  Issued one by one these are dependent global
+// loads (one round trip per 16-filter chunk); here they are asynchronous
+// copies into shared memory, issued ahead of their use: the mask words of
+// pixel i into s_mw[w * 128 + i], and the item's packed values (contiguous,
+// 16-byte aligned, a multiple of 4 floats) into `stage` when they fit.
+// Returns whether the values were staged (the same on every thread).
+constexpr int kMaxKW = 16;  // mask words per pixel, K <= 512
+__device__ __forceinline__ bool issue_row_copies(const Item &it, int a, int qa,
+                                                 const uint32_t *__restrict__ bits, int KW,
+                                                 const uint64_t *__restrict__ seg_base,
+                                                 const float *packed, float *stage,
+                                                 int stage_cap, uint32_t *s_mw) {
+  const int i = threadIdx.x;
+  const uint64_t sb = seg_base[qa];
+  const int cnt = (int)(seg_base[qa + 1] - sb);
+  const bool staged = cnt <= stage_cap;
+  if (staged)
+    for (int j = 4 * i; j < cnt; j += 4 * kThreads) tc::cp_async16(stage + j, packed + sb + j);
+  const int col = it.js * kStrip + i;
+  if (col < it.W) {
+    const uint32_t *w = bits + (it.base + (int64_t)a * it.W + col) * KW;
+    for (int k = 0; k < KW; ++k) tc::cp_async4(s_mw + k * kThreads + i, w + k, 4);
+  } else {
+    for (int k = 0; k < KW; ++k) s_mw[k * kThreads + i] = 0u;
+  }
+  tc::cp_async_commit();
+  return staged;
+}
+
+// 16-bit sampled mask of chunk c of this thread's pixel, from the staged words.
+__device__ __forceinline__ uint32_t staged_mask(const uint32_t *s_mw, int c) {
+  return (s_mw[(c >> 1) * kThreads + threadIdx.x] >> ((c & 1) * 16)) & 0xFFFFu;
+}
+
 // ------------------------------------------------------------------ synthesis
 
 template <int S>
@@ -340,10 +376,14 @@ struct SynthSmem {
   static constexpr int N = 16 * S;
   // A holds a_chunks filter chunks of 16 (4 KB each): all Kp / 16 where they
   // fit beside B, else the chunks are built and multiplied in groups
+  // Then B, the col2im rows, the staged packed values of one code row
+  // (stage_cap floats) and the staged mask words.
   __host__ __device__ static size_t a_bytes(int a_chunks) { return (size_t)a_chunks * 4096; }
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)N * Kp * 2; }
-  __host__ __device__ static size_t total(int Kp, int a_chunks) {
-    return 1024 + a_bytes(a_chunks) + b_bytes(Kp) + (size_t)2 * S * kPuRow * 4;
+  __host__ __device__ static size_t pu_bytes() { return (size_t)2 * S * kPuRow * 4; }
+  __host__ __device__ static size_t total(int Kp, int a_chunks, int stage_cap) {
+    return 1024 + a_bytes(a_chunks) + b_bytes(Kp) + pu_bytes() + (size_t)stage_cap * 4 +
+           (size_t)kMaxKW * kThreads * 4;
   }
 };
 
@@ -356,7 +396,8 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
                                                             const uint4 *__restrict__ bsyn,
                                                             float *__restrict__ xcore,
                                                             float *__restrict__ spill,
-                                                            int a_chunks, int *err) {
+                                                            int a_chunks, int stage_cap,
+                                                            int *err) {
   using L = SynthSmem<S>;
   constexpr int C = L::C, N = L::N;
   const int NC = Kp / 16;
@@ -365,6 +406,8 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
   uint8_t *As = smem;
   uint8_t *Bs = As + L::a_bytes(a_chunks);
   float *Pu = reinterpret_cast<float *>(Bs + L::b_bytes(Kp));  // [2][S][kPuRow]
+  float *stage = reinterpret_cast<float *>(Bs + L::b_bytes(Kp) + L::pu_bytes());
+  uint32_t *s_mw = reinterpret_cast<uint32_t *>(stage + stage_cap);
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
 
@@ -411,19 +454,25 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
     const bool halo = i < 2 * C;
     const int hcol = i < C ? i - C : kStrip + i - C;  // halo output column (strip-local)
 
+    // row a's copies are issued while row a-1 is multiplied and folded
+    bool staged = issue_row_copies(it, a_start, it.q_row0 + a_start, bits, KW, seg_base, packed,
+                                   stage, stage_cap, s_mw);
     for (int a = a_start; a < a_end; ++a) {
       const int qa = it.q_row0 + a;
-      const float *src = packed + seg_base[qa] + pxoff[(int64_t)qa * kStrip + i];
+      const uint32_t po = pxoff[(int64_t)qa * kStrip + i];
+      tc::cp_async_wait<0>();
+      __syncthreads();
+      const float *src = staged ? stage + po : packed + seg_base[qa] + po;
       for (int g0 = 0; g0 < NC; g0 += a_chunks) {
         const int g1 = min(NC, g0 + a_chunks);
         // 1. expand the packed codes of code row a (this thread: pixel i),
         // filter chunks g0 .. g1-1, into the A operand (BF16)
         for (int c = g0; c < g1; ++c) {
-          const uint32_t m = chunk_mask(bits, KW, it, a, b0 + i, c);
+          const uint32_t m = staged_mask(s_mw, c);
           float v[16];
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
-            v[e] = ((m >> e) & 1u) ? __ldg(src) : 0.0f;
+            v[e] = ((m >> e) & 1u) ? *src : 0.0f;
             src += (m >> e) & 1u;
           }
           uint4 lo = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
@@ -457,6 +506,10 @@ __global__ void __launch_bounds__(kThreads) synth_tc_kernel(ItemMap im, int K, i
         tc::fence_after_sync();
       }
       if (failed) break;
+      // every thread is past its reads of the staged row: fetch the next one
+      if (a + 1 < a_end)
+        staged = issue_row_copies(it, a + 1, qa + 1, bits, KW, seg_base, packed, stage, stage_cap,
+                                  s_mw);
       // 3. col2im: output row a-c+u gets sum_v P[b + c - v][(u, v)]
 #pragma unroll
       for (int u = 0; u < S; ++u) {
@@ -560,8 +613,11 @@ struct AdjSmem {
   static constexpr int C = (S - 1) / 2;
   static constexpr int kSRow = 17 * 128;  // one Toeplitz residual row (17 blocks)
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)S * Kp * 32; }
-  __host__ __device__ static size_t total(int Kp) {
-    return 1024 + b_bytes(Kp) + (size_t)S * kSRow + 144 * 4;
+  // B, the residual ring, its staging row, the staged packed values of one
+  // code row (stage_cap floats) and the staged mask words
+  __host__ __device__ static size_t total(int Kp, int stage_cap) {
+    return 1024 + b_bytes(Kp) + (size_t)S * kSRow + 144 * 4 + (size_t)stage_cap * 4 +
+           (size_t)kMaxKW * kThreads * 4;
   }
 };
 
@@ -580,7 +636,7 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
                                                           const uint4 *__restrict__ badj,
                                                           const float *__restrict__ r,
                                                           const StepParams *__restrict__ prm,
-                                                          int *err) {
+                                                          int stage_cap, int *err) {
   using L = AdjSmem<S>;
   constexpr int C = L::C;
   const int NC = Kp / 16;
@@ -590,6 +646,8 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
   uint8_t *Bs = smem;
   uint8_t *ring = Bs + L::b_bytes(Kp);
   float *rstage = reinterpret_cast<float *>(ring + (size_t)S * L::kSRow);
+  float *stage = rstage + 144;
+  uint32_t *s_mw = reinterpret_cast<uint32_t *>(stage + stage_cap);
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
 
@@ -654,7 +712,6 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
     const Item it0 = item_of(im, q);
     const int seg_end = min(q_end, it0.q_row0 + it0.H);
     const int o0 = it0.a, o1 = o0 + (seg_end - q);
-    const int b0 = it0.js * kStrip;
     for (int ar = o0 - C; ar < o0 + C; ++ar) build_row(it0, ar);
     for (int a = o0; a < o1; ++a) {
       const int qa = it0.q_row0 + a;
@@ -677,6 +734,11 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
         }
         tc::mma_commit(&mbar);
       }
+      // the row's packed values and mask words, copied while the MMAs run
+      const bool staged = issue_row_copies(it0, a, qa, bits, KW, seg_base, packed, stage,
+                                           stage_cap, s_mw);
+      const uint32_t po = pxoff[(int64_t)qa * kStrip + i];
+      tc::cp_async_wait<0>();
       bool ok = tc::mbar_wait_bounded(&mbar, phase, kWaitNs);
       phase ^= 1u;
       if (__syncthreads_or(!ok)) {
@@ -685,10 +747,11 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
         break;
       }
       tc::fence_after_sync();
-      // prox on the packed sampled codes of this item (this thread: pixel i)
-      float *dst = packed + seg_base[qa] + pxoff[(int64_t)qa * kStrip + i];
+      // prox on the packed sampled codes of this item (this thread: pixel i),
+      // in shared memory when staged
+      float *dst = (staged ? stage : packed + seg_base[qa]) + po;
       for (int c = 0; c < NC; ++c) {
-        const uint32_t m = chunk_mask(bits, KW, it0, a, b0 + i, c);
+        const uint32_t m = staged_mask(s_mw, c);
         float g[16];
         tc::tmem_ld16(lane_addr + 16 * c, g);
 #pragma unroll
@@ -701,6 +764,13 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
       }
       tc::fence_before_sync();
       __syncthreads();
+      if (staged) {
+        // the updated row back, coalesced
+        const uint64_t sb = seg_base[qa];
+        const int cnt = (int)(seg_base[qa + 1] - sb);
+        for (int j = 4 * tid; j < cnt; j += 4 * kThreads)
+          *reinterpret_cast<float4 *>(packed + sb + j) = *reinterpret_cast<const float4 *>(stage + j);
+      }
     }
     q = seg_end;
   }
@@ -1154,19 +1224,44 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
   const bool pipe_ok = tc_pipe_supported(K, s, ws.max_smem);
   const int fin_grid = std::min(Q, ws.sm_count * 16);  // finalize: blocks over row items
   // launch geometry of the single-stage kernels (several CTAs per SM)
-  int grid_s1 = 1, grid_a1 = 1, a_chunks = NC;
+  int grid_s1 = 1, grid_a1 = 1, a_chunks = NC, stage_s = 0, stage_a = 0;
   size_t smem_s1 = 0, smem_a1 = 0;
+  if (ws.smem_sm == 0) {
+    int dev;
+    TRY(cudaGetDevice(&dev));
+    TRY(cudaDeviceGetAttribute(&ws.smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  }
   TRY(dispatch_s(s, [&](auto SC) -> cudaError_t {
     constexpr int S = decltype(SC)::value;
-    // the synthesis keeps every filter chunk of a code row in shared memory
-    // where they fit beside the filters (1 KB left for static shared memory)
+    using SL = SynthSmem<S>;
+    using AL = AdjSmem<S>;
+    // 1 KB of each CTA's share is left for static shared memory and 1 KB is
+    // reserved by the system
     const size_t smem_cap = (size_t)ws.max_smem - 1024;
-    if (SynthSmem<S>::total(Kp, NC) > smem_cap) {
-      const size_t fixed = SynthSmem<S>::total(Kp, 0);
-      a_chunks = fixed < smem_cap ? (int)((smem_cap - fixed) / 4096) : 0;
-    }
-    smem_s1 = SynthSmem<S>::total(Kp, a_chunks);
-    smem_a1 = AdjSmem<S>::total(Kp);
+    auto per_cta = [&](int occ) {
+      return std::min(smem_cap, (size_t)ws.smem_sm / (size_t)occ - 2048);
+    };
+    // staged values of one code row: the expected count with a margin (rows
+    // above it are read in place)
+    const int want = (int)std::min(16384.0, ws.sample_p * K * kStrip * 1.25 + 512.0) & ~3;
+    // synthesis: as many CTAs per SM as its 256 TMEM columns allow where the
+    // filters and all chunks fit; the staging takes what is left, down to 8
+    // chunks in shared memory (the rest are built and multiplied in groups)
+    const size_t s_all = SL::total(Kp, NC, 0);
+    const int occ_s_t = std::max(1, std::min(2, (int)(ws.smem_sm / (s_all + 2048))));
+    const size_t cap_s = per_cta(occ_s_t);
+    const size_t s_keep = SL::total(Kp, std::min(NC, 8), 0);
+    stage_s = cap_s > s_keep ? (int)std::min<size_t>(want, (cap_s - s_keep) / 4) & ~3 : 0;
+    const size_t s_fixed = SL::total(Kp, 0, stage_s);
+    a_chunks = s_fixed < cap_s ? std::min(NC, (int)((cap_s - s_fixed) / 4096)) : 0;
+    smem_s1 = SL::total(Kp, a_chunks, stage_s);
+    // adjoint: the CTAs per SM its TMEM columns and unstaged layout allow
+    const size_t a_min = AL::total(Kp, 0);
+    const int occ_a_t = std::max(
+        1, std::min(512 / tmem_cols_for(Kp), (int)(ws.smem_sm / (a_min + 2048))));
+    const size_t cap_a = per_cta(occ_a_t);
+    stage_a = cap_a > a_min ? (int)std::min<size_t>(want, (cap_a - a_min) / 4) & ~3 : 0;
+    smem_a1 = AL::total(Kp, stage_a);
     if (a_chunks < 1 || smem_a1 > smem_cap) {
       ws.last_error = "the filters do not fit in shared memory";
       return cudaErrorNotSupported;
@@ -1214,7 +1309,7 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
         constexpr int S = decltype(SC)::value;
         synth_tc_kernel<S><<<grid_s1, kThreads, smem_s1, st>>>(
             im, K, Kp, KW, bits, seg_base, pxoff, as<float>(ws.packed), as<uint4>(ws.bsyn),
-            as<float>(ws.xcore), as<float>(ws.spill), a_chunks, as<int>(ws.err));
+            as<float>(ws.xcore), as<float>(ws.spill), a_chunks, stage_s, as<int>(ws.err));
         return cudaGetLastError();
       }));
     }
@@ -1244,7 +1339,7 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
         constexpr int S = decltype(SC)::value;
         adj_tc_kernel<S><<<grid_a1, kThreads, smem_a1, st>>>(
             im, K, Kp, KW, bits, seg_base, pxoff, as<float>(ws.packed), as<uint4>(ws.badj),
-            as<float>(ws.r), prm, as<int>(ws.err));
+            as<float>(ws.r), prm, stage_a, as<int>(ws.err));
         return cudaGetLastError();
       }));
     }
@@ -1324,6 +1419,9 @@ cudaError_t tc_code_step(TcWorkspace &ws, const BatchDev &b, const int *H_host, 
     gk.Q = Q;
     gk.variant = variant;
     gk.iters = rem;
+    gk.a_chunks = a_chunks;
+    gk.stage_s = stage_s;
+    gk.stage_a = stage_a;
     TRY(replay_graph(ws, gk, rem, [&](int) { return iteration(variant); }, st));
   } else {
     for (int it = 0; it < rem; ++it) TRY(iteration(variant));

@@ -28,6 +28,7 @@ struct GraphKey {
   const void *v16a, *v16b, *idx16, *xcore2, *spill2;  // fused path
   int64_t total_px;
   int n_images, K, s, Q, variant, iters;
+  int a_chunks, stage_s, stage_a;  // shared-memory layout of the single-stage kernels
 };
 
 // A few captured graphs, reused while their key matches (the host-buffer
@@ -55,6 +56,7 @@ struct TcWorkspace {
   int n_items = 0;
   int sm_count = 0;
   int max_smem = 0;
+  int smem_sm = 0;  // shared memory per SM
   Profiler *prof = nullptr;  // the owning context's profiler
   bool autotune = true, graphs = true, fused = true;
   // sampling rate p of the code step (set by the caller before each call):

@@ -3,10 +3,10 @@
 //
 // Row item q: image row a of the 128-column strip js of image n; items are
 // ordered (n, js, a), item0[n] is the first item of image n.  The sampled
-// codes of item q are stored chunk-major from seg_base[q * NC]: for each
-// 16-filter chunk c the values of the item's 128 pixels in pixel order, each
-// pixel's in filter order.  Every item's storage is padded to a multiple of
-// 4 floats so that it starts 16-byte aligned.
+// codes of item q are stored pixel-major from seg_base[q]: the values of
+// pixel p, in filter order, start at seg_base[q] + pxoff[q * 128 + p].  Every
+// item's storage is padded to a multiple of 4 floats (8 for the BF16 codes
+// of the fused kernel) so that it starts 16-byte aligned.
 #pragma once
 #include "scsc_internal.cuh"
 
