@@ -105,31 +105,112 @@ __global__ void surrogate_b_kernel(BatchDev b, int K, int S, const float *__rest
   if (threadIdx.x == 0) Bv[col] = alpha * Bv[col] + beta * red[0];
 }
 
-// out[a] = sum_b C[a][b] v[b] (- Bv[a]), one warp per row.  Each lane keeps
-// four FP32 partial sums over runs of 128 products (FP32 FMAs: this GPU's FP64
-// rate would make the product FMA-bound instead of bandwidth-bound) and folds
-// each run into an FP64 total, which the warp reduces in FP64.
-template <bool kGrad>
-__global__ void symv_kernel(const float *__restrict__ Cm, int64_t n, const float *__restrict__ v,
-                            const double *__restrict__ Bv, float *__restrict__ outf,
-                            double *__restrict__ outd) {
-  int64_t row = blockIdx.x * (int64_t)(blockDim.x / 32) + threadIdx.x / 32;
-  int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  const float *cr = Cm + row * n;
-  double s = 0.0;
-  for (int64_t j0 = 0; j0 < n; j0 += 32 * 128) {
-    float p[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    const int64_t j1 = j0 + 32 * 128 < n ? j0 + 32 * 128 : n;
-#pragma unroll 4
-    for (int64_t j = j0 + lane; j < j1; j += 32) p[(j >> 5) & 3] = fmaf(cr[j], v[j], p[(j >> 5) & 3]);
-    s += ((double)p[0] + (double)p[1]) + ((double)p[2] + (double)p[3]);
-  }
+// out = C v (- Bv) for the symmetric C, reading its upper block triangle
+// only.  C is cut into panels of kSymB rows and columns; CTA b takes block
+// (I, J), J >= I, of the upper triangle (row by row).  It writes the block's
+// row products C_IJ v_J (rows of panel I) into slot J of panel I and, off the
+// diagonal, its column products C_IJ^T v_I (rows of panel J) into slot I of
+// panel J, so every (slot, row) of the partial buffer part[NP][n] is written
+// exactly once.  The partials are FP32 sums of at most kSymB products; the
+// reduction sums a row's NP slots in FP64 in a fixed order.
+constexpr int kSymB = 128;
+
+__device__ __forceinline__ int64_t upper_offset(int64_t I, int64_t NP) {
+  return I * NP - I * (I - 1) / 2;  // blocks in the triangle's rows 0 .. I-1
+}
+
+template <bool kVec>
+__global__ void __launch_bounds__(256) symv_upper_kernel(const float *__restrict__ Cm, int64_t n,
+                                                         int NP, const float *__restrict__ v,
+                                                         float *__restrict__ part) {
+  __shared__ float s_col[8][kSymB];
+  const int64_t b = blockIdx.x;
+  // row I of the triangle holding block b: the root of offset(I) = b, then
+  // corrected against the exact integer offsets
+  const double tn = 2.0 * NP + 1.0;
+  int64_t I = (int64_t)((tn - sqrt(tn * tn - 8.0 * (double)b)) * 0.5);
+  if (I < 0) I = 0;
+  if (I > NP - 1) I = NP - 1;
+  while (I > 0 && upper_offset(I, NP) > b) --I;
+  while (I + 1 < NP && upper_offset(I + 1, NP) <= b) ++I;
+  const int64_t J = I + (b - upper_offset(I, NP));
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t r0 = I * kSymB, c0 = J * kSymB + 4 * lane;
+  float vj[4];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) {
-    if (kGrad) outd[row] = s - Bv[row];
-    else outf[row] = (float)s;
+  for (int q = 0; q < 4; ++q) vj[q] = c0 + q < n ? v[c0 + q] : 0.0f;
+  // rows r0 + w + 8 k, k < 16; this lane's 4 columns c0 .. c0 + 3
+  float4 c[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int64_t r = r0 + w + 8 * k;
+    c[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (r < n) {
+      const float *src = Cm + r * n + c0;
+      if (kVec) {
+        if (c0 < n) c[k] = *reinterpret_cast<const float4 *>(src);
+      } else {
+        if (c0 < n) c[k].x = src[0];
+        if (c0 + 1 < n) c[k].y = src[1];
+        if (c0 + 2 < n) c[k].z = src[2];
+        if (c0 + 3 < n) c[k].w = src[3];
+      }
+    }
+  }
+  float col[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int64_t r = r0 + w + 8 * k;
+    const float vi = r < n ? v[r] : 0.0f;
+    float rp = c[k].x * vj[0];
+    rp = fmaf(c[k].y, vj[1], rp);
+    rp = fmaf(c[k].z, vj[2], rp);
+    rp = fmaf(c[k].w, vj[3], rp);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rp += __shfl_xor_sync(0xffffffffu, rp, o);
+    if (lane == k && r < n) part[J * n + r] = rp;
+    col[0] = fmaf(c[k].x, vi, col[0]);
+    col[1] = fmaf(c[k].y, vi, col[1]);
+    col[2] = fmaf(c[k].z, vi, col[2]);
+    col[3] = fmaf(c[k].w, vi, col[3]);
+  }
+  if (I == J) return;  // whole CTA: the diagonal block's rows cover it
+#pragma unroll
+  for (int q = 0; q < 4; ++q) s_col[w][4 * lane + q] = col[q];
+  __syncthreads();
+  if (threadIdx.x < kSymB) {
+    float sum = 0.0f;
+#pragma unroll
+    for (int ww = 0; ww < 8; ++ww) sum += s_col[ww][threadIdx.x];
+    const int64_t cc = J * kSymB + threadIdx.x;
+    if (cc < n) part[I * n + cc] = sum;
+  }
+}
+
+// out[i] = sum over the NP slots of part[.][i] in FP64 (- Bv[i]).  Block
+// (32, 8): x over 32 consecutive rows, y over the slots y, y + 8, ...; the 8
+// partial sums are added in a fixed order.
+template <bool kGrad>
+__global__ void __launch_bounds__(256) symv_reduce_kernel(const float *__restrict__ part,
+                                                          int64_t n, int NP,
+                                                          const double *__restrict__ Bv,
+                                                          float *__restrict__ outf,
+                                                          double *__restrict__ outd) {
+  __shared__ double s_sum[8][33];
+  const int64_t i = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  double acc = 0.0;
+  if (i < n) {
+#pragma unroll 4
+    for (int sl = threadIdx.y; sl < NP; sl += 8) acc += (double)part[(int64_t)sl * n + i];
+  }
+  s_sum[threadIdx.y][threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.y == 0 && i < n) {
+    double t = 0.0;
+#pragma unroll
+    for (int y = 0; y < 8; ++y) t += s_sum[y][threadIdx.x];
+    if (kGrad) outd[i] = t - Bv[i];
+    else outf[i] = (float)t;
   }
 }
 
@@ -413,19 +494,33 @@ cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, cons
   return cudaGetLastError();
 }
 
-cudaError_t launch_symv(const float *Cm, int64_t n, const float *v, const double *unused, float *out,
-                        cudaStream_t st) {
-  (void)unused;
-  int64_t blocks = (n + 7) / 8;
-  symv_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(Cm, n, v, nullptr, out, nullptr);
+int symv_panels(int64_t n) { return (int)((n + kSymB - 1) / kSymB); }
+
+template <bool kGrad>
+static cudaError_t symv_both(const float *Cm, int64_t n, const float *v, const double *Bv,
+                             float *outf, double *outd, float *part, cudaStream_t st) {
+  const int NP = symv_panels(n);
+  const int64_t nblocks = (int64_t)NP * (NP + 1) / 2;
+  if (nblocks > 0x7fffffff) return cudaErrorInvalidValue;
+  if (n % 4 == 0)
+    symv_upper_kernel<true><<<(unsigned)nblocks, 256, 0, st>>>(Cm, n, NP, v, part);
+  else
+    symv_upper_kernel<false><<<(unsigned)nblocks, 256, 0, st>>>(Cm, n, NP, v, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  symv_reduce_kernel<kGrad><<<(unsigned)((n + 31) / 32), dim3(32, 8), 0, st>>>(part, n, NP, Bv,
+                                                                               outf, outd);
   return cudaGetLastError();
 }
 
+cudaError_t launch_symv(const float *Cm, int64_t n, const float *v, float *out, float *part,
+                        cudaStream_t st) {
+  return symv_both<false>(Cm, n, v, nullptr, out, nullptr, part, st);
+}
+
 cudaError_t launch_symv_grad(const float *Cm, int64_t n, const float *d, const double *Bv,
-                             double *out, cudaStream_t st) {
-  int64_t blocks = (n + 7) / 8;
-  symv_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(Cm, n, d, Bv, nullptr, out);
-  return cudaGetLastError();
+                             double *out, float *part, cudaStream_t st) {
+  return symv_both<true>(Cm, n, d, Bv, nullptr, out, part, st);
 }
 
 cudaError_t launch_double_to_float(const double *in, float *out, int n, cudaStream_t st) {

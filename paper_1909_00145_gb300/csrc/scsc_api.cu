@@ -108,6 +108,7 @@ struct scsc_ctx {
   bool sp_use = false;
   // online surrogates
   DevBuf C, B, Cd;
+  DevBuf Cpart;  // partial sums of the products with C
   uint64_t online_t = 0;
   Profiler prof;
 };
@@ -561,7 +562,10 @@ scsc_status scsc_destroy(scsc_ctx *ctx) {
                     &ctx->xkeep, &ctx->zkeep, &ctx->bits_off,
                     &ctx->hd, &ctx->hx[0], &ctx->hx[1], &ctx->hz[0], &ctx->hz[1],
                     &ctx->C, &ctx->B, &ctx->Cd, &ctx->batch.dev, &ctx->domain.dev,
-                    &ctx->sg, &ctx->spref, &ctx->snrm, &ctx->spart, &ctx->simg, &ctx->skept})
+                    &ctx->sg, &ctx->spref, &ctx->snrm, &ctx->spart, &ctx->simg, &ctx->skept,
+                    &ctx->sp_cpx, &ctx->sp_ckt, &ctx->sp_row, &ctx->sp_kt, &ctx->sp_scan,
+                    &ctx->sp_pk, &ctx->sp_pv, &ctx->sp_kpix, &ctx->sp_kimg, &ctx->sp_kv,
+                    &ctx->sp_T, &ctx->Cpart})
     b->release();
   if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
   for (BatchCache *bc : {&ctx->batch, &ctx->domain}) {
@@ -1132,14 +1136,17 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
                                     ctx->B.as<double>(), st);
   ctx->sp_use = false;
   CK(e);
+  CK(ctx->Cpart.ensure((size_t)symv_panels(KM) * KM * 4));
+  float *cpart = ctx->Cpart.as<float>();
   CKS(power_iteration(ctx, KM, kTagLc,
                       [&](const float *u, float *w) -> scsc_status {
-                        CK(launch_symv(ctx->C.as<float>(), KM, u, nullptr, w, ctx->stream));
+                        CK(launch_symv(ctx->C.as<float>(), KM, u, w, cpart, ctx->stream));
                         return SCSC_OK;
                       },
                       2, nullptr, 0.0));
   // grad = C d - B (FP64 accumulation), then the projected step
-  CK(launch_symv_grad(ctx->C.as<float>(), KM, d_dev, ctx->B.as<double>(), ctx->Cd.as<double>(), st));
+  CK(launch_symv_grad(ctx->C.as<float>(), KM, d_dev, ctx->B.as<double>(), ctx->Cd.as<double>(),
+                      cpart, st));
   CK(launch_project_step(d_dev, nullptr, ctx->Cd.as<double>(), ctx->scal.as<double>() + 2, K, M, st));
   ctx->online_t = t;
   return SCSC_OK;

@@ -122,10 +122,14 @@ cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, cons
 // Floats of the correlation buffer T of that update (K * K * (2s-1)^2); with
 // T == nullptr the update walks every patch instead (no buffer).
 size_t surrogate_corr_floats(int K, int s);
-cudaError_t launch_symv(const float *Cm, int64_t n, const float *v, const double *unused,
-                        float *out, cudaStream_t st);
+// out = C v (FP32 out) and out = C d - B (FP64 out) for the symmetric C of
+// order n, from its upper block triangle; part holds symv_panels(n) * n
+// floats of partial sums.
+int symv_panels(int64_t n);
+cudaError_t launch_symv(const float *Cm, int64_t n, const float *v, float *out, float *part,
+                        cudaStream_t st);
 cudaError_t launch_symv_grad(const float *Cm, int64_t n, const float *d, const double *Bv,
-                             double *out, cudaStream_t st);
+                             double *out, float *part, cudaStream_t st);
 cudaError_t launch_double_to_float(const double *in, float *out, int n, cudaStream_t st);
 cudaError_t launch_set_step(StepParams *prm, double step, double lambda, cudaStream_t st);
 

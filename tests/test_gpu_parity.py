@@ -333,12 +333,16 @@ def test_dict_step_online_k64_s11():
     assert np.all(np.linalg.norm(host(dt).reshape(K, -1), axis=1) <= 1 + 1e-6)
 
 
-@pytest.mark.parametrize("K,s,density", [(400, 3, 0.01), (48, 7, 0.02), (48, 7, 0.1)])
+@pytest.mark.parametrize("K,s,density", [(400, 3, 0.01), (48, 7, 0.02), (48, 7, 0.1),
+                                         (27, 5, 0.04)])
 def test_dict_step_online_surrogate_paths(K, s, density):
     """Eq. 7-8 over three streamed mini-batches against the oracle.  Codes
     sparser than 1/16 update the surrogates from the nonzero codes only (K =
     400, the filter count of the paper's large online runs, at s = 3; K = 48 at
-    s = 7); denser ones through the dense implicit GEMM (density 0.1)."""
+    s = 7); denser ones through the dense implicit GEMM (density 0.1).  The
+    products with C read its upper 128 x 128 block triangle; K = 27, s = 5
+    gives an order (675) that is not a multiple of 4 (unvectorised rows) with
+    a ragged last panel."""
     H, W = [16, 12], [20, 18]
     cfg = R.Config(K=K, s=s, seed=13)
     st = R.OnlineState(cfg)
