@@ -6,7 +6,10 @@
 //     C <- a C + b sum_n Z_n^T Z_n,     B <- a B + b sum_n Z_n^T x_n
 // is an implicit GEMM over all pixels of the batch: Z is never materialised,
 // its entries are gathered from the codes while staging tiles in shared memory.
+#include <algorithm>
+
 #include "scsc_internal.cuh"
+#include "scsc_tc.cuh"
 
 namespace scsc {
 
@@ -285,21 +288,51 @@ __global__ void __launch_bounds__(256) surrogate_sparse_kernel(
 // Entry ((k,u,v),(k2,u2,v2)) of sum_q Z[q]^T Z[q] is T[k][k2][u-u2][v-v2]
 // minus the products whose patch centre q = r1 - c + (u,v) lies outside the
 // image (only codes within c of the border have such q; surrogate_border_
-// kernel subtracts them).  Block k, thread = lag: each thread owns its lag's
-// entries of row block k and walks filter k's nonzeros in order, so the sums
-// are deterministic without barriers or atomics.
+// kernel subtracts them).
+// The nonzeros of a filter are cut into segments of seg_len (how many codes
+// each filter holds varies widely, and a filter's walk is sequential); block
+// = segment, thread = lag.  Each thread walks its segment in order into the
+// segment's own slice (T itself for a filter of one segment), and
+// corr_reduce_kernel adds a filter's slices in segment order, so the sums
+// are deterministic without atomics.
+
+// seg_off[k] = first segment of filter k, seg_off[K] = segment count.
+__global__ void corr_segments_kernel(const int64_t *__restrict__ kt_off, int ntiles, int K,
+                                     int seg_len, int *__restrict__ seg_off) {
+  if (threadIdx.x != 0) return;
+  int run = 0;
+  for (int k = 0; k < K; ++k) {
+    const int64_t cnt = kt_off[(int64_t)(k + 1) * ntiles] - kt_off[(int64_t)k * ntiles];
+    seg_off[k] = run;
+    run += (int)((cnt + seg_len - 1) / seg_len);
+  }
+  seg_off[K] = run;
+}
+
 __global__ void __launch_bounds__(512) surrogate_corr_kernel(
     BatchDev b, int K, int S, const int64_t *__restrict__ row_ptr, const int *__restrict__ pk,
     const float *__restrict__ pv, const int64_t *__restrict__ kt_off, int ntiles,
     const int *__restrict__ kpix, const int *__restrict__ kimg, const float *__restrict__ kv,
-    float *__restrict__ T) {
-  const int k = blockIdx.x, D = 2 * S - 1, DD = D * D, t = threadIdx.x;
-  if (t >= DD) return;
+    const int *__restrict__ seg_off, int seg_len, float *__restrict__ P, float *__restrict__ T) {
+  const int seg = blockIdx.x, D = 2 * S - 1, DD = D * D, t = threadIdx.x;
+  if (seg >= seg_off[K] || t >= DD) return;
+  // the filter of this segment: the last k with seg_off[k] <= seg (filters
+  // without segments share their offset with the next one)
+  int lo = 0, hi = K - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (seg_off[mid] <= seg) lo = mid;
+    else hi = mid - 1;
+  }
+  const int k = lo;
   const int dy = t / D - (S - 1), dx = t - (t / D) * D - (S - 1);
-  float *const Tk = T + (int64_t)k * K * DD;
-  for (int k2 = k; k2 < K; ++k2) Tk[(int64_t)k2 * DD + t] = 0.0f;
   const int64_t kb = kt_off[(int64_t)k * ntiles], ke = kt_off[(int64_t)(k + 1) * ntiles];
-  for (int64_t e = kb; e < ke; ++e) {
+  const int64_t e0 = kb + (int64_t)(seg - seg_off[k]) * seg_len;
+  const int64_t e1 = e0 + seg_len < ke ? e0 + seg_len : ke;
+  float *const Tk = (seg_off[k + 1] - seg_off[k] == 1 ? T + (int64_t)k * K * DD
+                                                      : P + (int64_t)seg * K * DD);
+  for (int k2 = k; k2 < K; ++k2) Tk[(int64_t)k2 * DD + t] = 0.0f;
+  for (int64_t e = e0; e < e1; ++e) {
     const int n = kimg[e];
     const int H = b.H[n], W = b.W[n];
     const int64_t base = b.off[n];
@@ -313,6 +346,22 @@ __global__ void __launch_bounds__(512) surrogate_corr_kernel(
       if (k2 >= k) Tk[(int64_t)k2 * DD + t] += z1 * pv[e2];
     }
   }
+}
+
+// T[k][k2 >= k][.] of the filters without a single segment: the sum of their
+// segments' slices in segment order, or zero for a filter without nonzeros.
+__global__ void __launch_bounds__(256) corr_reduce_kernel(const float *__restrict__ P,
+                                                          const int *__restrict__ seg_off, int K,
+                                                          int DD, float *__restrict__ T) {
+  const int k = blockIdx.y;
+  const int s0 = seg_off[k], s1 = seg_off[k + 1];
+  if (s1 - s0 == 1) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)(K - k) * DD) return;
+  const int64_t off = (int64_t)k * DD + i;  // k2 * DD + lag, k2 >= k
+  float acc = 0.0f;
+  for (int sg = s0; sg < s1; ++sg) acc += P[(int64_t)sg * K * DD + off];
+  T[(int64_t)k * K * DD + off] = acc;
 }
 
 // C[a][b] <- alpha C[a][b] + beta T[k][k2][u-u2][v-v2] over the columns b of
@@ -460,20 +509,39 @@ size_t surrogate_corr_floats(int K, int s) {
   return (size_t)K * K * D * D;
 }
 
+// Segment length and slice count of the correlation walk for nnz nonzero
+// codes: segments of 1024 nonzeros, longer where the slices would pass 4 GB.
+void surrogate_corr_segments(int K, int s, int64_t nnz, int *seg_len, int64_t *max_segments) {
+  const int64_t D = 2 * s - 1, slice = (int64_t)K * D * D * 4;
+  const int64_t budget = std::max<int64_t>(K + 1, ((int64_t)4 << 30) / slice);
+  int64_t len = 1024;
+  if (nnz / len + K > budget) len = (nnz + (budget - K) - 1) / (budget - K);
+  *seg_len = (int)std::min<int64_t>(len, 0x7fffffff);
+  *max_segments = nnz / *seg_len + K;
+}
+
 cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, const float *x,
                                            const int64_t *row_ptr, const int *pk, const float *pv,
                                            const int64_t *kt_off, const int *kpix,
                                            const int *kimg, const float *kv, double alpha,
                                            double beta, float *Cm, double *Bv, float *T,
-                                           cudaStream_t st) {
+                                           const CorrSegments *segs, cudaStream_t st) {
   const int KM = K * s * s;
   const int nt_px = sparse_tiles(b.total_px);
   cudaError_t e;
   if (T != nullptr) {
     // correlations, then C = alpha C + beta T (upper blocks), then the
     // border corrections and B
-    surrogate_corr_kernel<<<K, 512, 0, st>>>(b, K, s, row_ptr, pk, pv, kt_off, nt_px, kpix, kimg,
-                                             kv, T);
+    if (segs == nullptr || segs->max_segments > 0x7fffffff) return cudaErrorInvalidValue;
+    corr_segments_kernel<<<1, 32, 0, st>>>(kt_off, nt_px, K, segs->seg_len, segs->seg_off);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    surrogate_corr_kernel<<<(unsigned)segs->max_segments, 512, 0, st>>>(
+        b, K, s, row_ptr, pk, pv, kt_off, nt_px, kpix, kimg, kv, segs->seg_off, segs->seg_len,
+        segs->P, T);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int DD = (2 * s - 1) * (2 * s - 1);
+    corr_reduce_kernel<<<dim3((unsigned)(((int64_t)K * DD + 255) / 256), K), 256, 0, st>>>(
+        segs->P, segs->seg_off, K, DD, T);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     surrogate_expand_kernel<<<KM, 256, 0, st>>>(Cm, T, K, s, (float)alpha, (float)beta);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

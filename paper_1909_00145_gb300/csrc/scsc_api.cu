@@ -105,6 +105,8 @@ struct scsc_ctx {
   // pixel-major and filter-major entries (kernels_sparse.cu)
   DevBuf sp_cpx, sp_ckt, sp_row, sp_kt, sp_scan, sp_pk, sp_pv, sp_kpix, sp_kimg, sp_kv;
   DevBuf sp_T;  // cross-correlations of the code maps (online surrogate update)
+  DevBuf sp_seg, sp_P;  // their segment offsets and per-segment slices
+  int64_t sp_nnz = 0;   // entries of the index
   bool sp_use = false;
   // online surrogates
   DevBuf C, B, Cd;
@@ -369,6 +371,7 @@ scsc_status build_sparse(scsc_ctx *ctx, const float *z) {
                      cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (nnz * 16 > b.total_px * (int64_t)K) return SCSC_OK;
+  ctx->sp_nnz = nnz;
   const size_t n1 = (size_t)std::max<int64_t>(nnz, 1);
   CK(ctx->sp_pk.ensure(n1 * 4));
   CK(ctx->sp_pv.ensure(n1 * 4));
@@ -565,7 +568,7 @@ scsc_status scsc_destroy(scsc_ctx *ctx) {
                     &ctx->sg, &ctx->spref, &ctx->snrm, &ctx->spart, &ctx->simg, &ctx->skept,
                     &ctx->sp_cpx, &ctx->sp_ckt, &ctx->sp_row, &ctx->sp_kt, &ctx->sp_scan,
                     &ctx->sp_pk, &ctx->sp_pv, &ctx->sp_kpix, &ctx->sp_kimg, &ctx->sp_kv,
-                    &ctx->sp_T, &ctx->Cpart})
+                    &ctx->sp_T, &ctx->sp_seg, &ctx->sp_P, &ctx->Cpart})
     b->release();
   if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
   for (BatchCache *bc : {&ctx->batch, &ctx->domain}) {
@@ -1121,9 +1124,15 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
   CKS(build_sparse(ctx, z_dev));
   const double decay = (double)(t - 1) / (double)t, w_new = 1.0 / ((double)t * b.n);
   float *sp_corr = nullptr;  // the correlation buffer of the sparse update
+  CorrSegments segs{};
   if (ctx->sp_use) {
     CK(ctx->sp_T.ensure(surrogate_corr_floats(K, s) * 4));
     sp_corr = ctx->sp_T.as<float>();
+    surrogate_corr_segments(K, s, ctx->sp_nnz, &segs.seg_len, &segs.max_segments);
+    CK(ctx->sp_seg.ensure((size_t)(K + 1) * 4));
+    CK(ctx->sp_P.ensure((size_t)segs.max_segments * (surrogate_corr_floats(K, s) / K) * 4));
+    segs.seg_off = ctx->sp_seg.as<int>();
+    segs.P = ctx->sp_P.as<float>();
   }
   cudaError_t e =
       ctx->sp_use
@@ -1131,7 +1140,7 @@ scsc_status scsc_dict_step(scsc_ctx *ctx, const scsc_batch *batch, const float *
                 b, K, s, x_dev, ctx->sp_row.as<int64_t>(), ctx->sp_pk.as<int>(),
                 ctx->sp_pv.as<float>(), ctx->sp_kt.as<int64_t>(), ctx->sp_kpix.as<int>(),
                 ctx->sp_kimg.as<int>(), ctx->sp_kv.as<float>(), decay, w_new, ctx->C.as<float>(),
-                ctx->B.as<double>(), sp_corr, st)
+                ctx->B.as<double>(), sp_corr, &segs, st)
           : launch_surrogate_update(b, K, s, z_dev, x_dev, decay, w_new, ctx->C.as<float>(),
                                     ctx->B.as<double>(), st);
   ctx->sp_use = false;

@@ -111,6 +111,16 @@ bool tc_pipe_supported(int K, int s, int max_smem);
 cudaError_t launch_surrogate_update(const BatchDev &b, int K, int s, const float *z, const float *x,
                                     double alpha, double beta, float *Cm, double *Bv,
                                     cudaStream_t st);
+// The correlations walk each filter's nonzeros in segments of seg_len, each
+// into its own slice of P (max_segments slices of K * (2s-1)^2 floats);
+// seg_off holds K + 1 ints.
+struct CorrSegments {
+  int seg_len;
+  int64_t max_segments;
+  int *seg_off;
+  float *P;
+};
+void surrogate_corr_segments(int K, int s, int64_t nnz, int *seg_len, int64_t *max_segments);
 // The same update from the index of the nonzero codes (dictionary-step index
 // of kernels_sparse.cu), O(nnz * patch nonzeros) instead of O(D (K s^2)^2).
 cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, const float *x,
@@ -118,7 +128,7 @@ cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, cons
                                            const int64_t *kt_off, const int *kpix,
                                            const int *kimg, const float *kv, double alpha,
                                            double beta, float *Cm, double *Bv, float *T,
-                                           cudaStream_t st);
+                                           const CorrSegments *segs, cudaStream_t st);
 // Floats of the correlation buffer T of that update (K * K * (2s-1)^2); with
 // T == nullptr the update walks every patch instead (no buffer).
 size_t surrogate_corr_floats(int K, int s);

@@ -361,6 +361,36 @@ def test_dict_step_online_surrogate_paths(K, s, density):
         assert rel_l2(host(dt), d_o) < 1e-5
 
 
+def test_dict_step_online_skewed_filter_use():
+    """Eq. 7-8 with one filter far more used than the rest (about 1,600
+    nonzeros, so the correlation walk over its codes runs in two segments whose
+    slices are added), one filter not used at all (its correlations are zero)
+    and the others at 1%, over two streamed mini-batches."""
+    K, s, H, W = 20, 5, [40, 40], [40, 40]
+    cfg = R.Config(K=K, s=s, seed=17)
+    st = R.OnlineState(cfg)
+    ctx = scsc.Context(K, s, seed=17)
+    b = scsc.Batch(H, W)
+    rb = R.Batch(H=H, W=W, ids=[0, 1])
+    _, d, _ = make_case(H, W, K, s, seed=71)
+    dt = dev(d)
+    d_o = d.astype(np.float64).ravel()
+    rng = np.random.default_rng(5)
+    for t in range(1, 3):
+        x, _, z = make_case(H, W, K, s, seed=80 + t, code_density=0.01)
+        z = z.reshape(-1, K)
+        heavy = rng.random(z.shape[0]) < 0.5
+        z[:, 0] = np.where(heavy, rng.standard_normal(z.shape[0]), 0.0).astype(np.float32)
+        z[:, K - 1] = 0.0
+        z = np.ascontiguousarray(z.ravel())
+        assert np.count_nonzero(z[0::K]) > 1024 and (z != 0).mean() * 16 < 1
+        st.update(rb, x, z)
+        d_o = st.dict_step(d_o)
+        ctx.dict_step(b, dev(x), dev(z), dt, scsc.SCSC_DICT_ONLINE, t)
+        measured(f"online_skewed_t{t}", rel=rel_l2(host(dt), d_o))
+        assert rel_l2(host(dt), d_o) < 1e-5
+
+
 def test_code_step_bf16_large_k_fallback_kernels():
     """128 < K <= 256 runs the single-stage tensor kernels."""
     zg, zo, fg, fo, _ = run_code_step("bf16", 150, 5, [20, 9], [70, 140], (1, 4), 6, seed=4, lam=0.6)
