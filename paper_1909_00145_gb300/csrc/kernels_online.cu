@@ -510,11 +510,11 @@ size_t surrogate_corr_floats(int K, int s) {
 }
 
 // Segment length and slice count of the correlation walk for nnz nonzero
-// codes: segments of 1024 nonzeros, longer where the slices would pass 4 GB.
+// codes: segments of 256 nonzeros, longer where the slices would pass 4 GB.
 void surrogate_corr_segments(int K, int s, int64_t nnz, int *seg_len, int64_t *max_segments) {
   const int64_t D = 2 * s - 1, slice = (int64_t)K * D * D * 4;
   const int64_t budget = std::max<int64_t>(K + 1, ((int64_t)4 << 30) / slice);
-  int64_t len = 1024;
+  int64_t len = 256;
   if (nnz / len + K > budget) len = (nnz + (budget - K) - 1) / (budget - K);
   *seg_len = (int)std::min<int64_t>(len, 0x7fffffff);
   *max_segments = nnz / *seg_len + K;

@@ -363,9 +363,9 @@ def test_dict_step_online_surrogate_paths(K, s, density):
 
 def test_dict_step_online_skewed_filter_use():
     """Eq. 7-8 with one filter far more used than the rest (about 1,600
-    nonzeros, so the correlation walk over its codes runs in two segments whose
-    slices are added), one filter not used at all (its correlations are zero)
-    and the others at 1%, over two streamed mini-batches."""
+    nonzeros, so the correlation walk over its codes runs in several segments
+    whose slices are added), one filter not used at all (its correlations are
+    zero) and the others at 1%, over two streamed mini-batches."""
     K, s, H, W = 20, 5, [40, 40], [40, 40]
     cfg = R.Config(K=K, s=s, seed=17)
     st = R.OnlineState(cfg)
