@@ -614,10 +614,11 @@ struct AdjSmem {
   static constexpr int kSRow = 17 * 128;  // one Toeplitz residual row (17 blocks)
   __host__ __device__ static size_t b_bytes(int Kp) { return (size_t)S * Kp * 32; }
   // B, the residual ring, its staging row, the staged packed values of one
-  // code row (stage_cap floats) and the staged mask words
+  // code row (stage_cap floats), the staged mask words and the prox's
+  // gradient scratch
   __host__ __device__ static size_t total(int Kp, int stage_cap) {
     return 1024 + b_bytes(Kp) + (size_t)S * kSRow + 144 * 4 + (size_t)stage_cap * 4 +
-           (size_t)kMaxKW * kThreads * 4;
+           (size_t)kMaxKW * kThreads * 4 + (size_t)16 * kThreads * 4;
   }
 };
 
@@ -648,6 +649,7 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
   float *rstage = reinterpret_cast<float *>(ring + (size_t)S * L::kSRow);
   float *stage = rstage + 144;
   uint32_t *s_mw = reinterpret_cast<uint32_t *>(stage + stage_cap);
+  float *s_g = reinterpret_cast<float *>(s_mw + kMaxKW * kThreads);  // [16][kThreads]
   __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_base;
 
@@ -749,15 +751,30 @@ __global__ void __launch_bounds__(kThreads) adj_tc_kernel(ItemMap im, int K, int
       tc::fence_after_sync();
       // prox on the packed sampled codes of this item (this thread: pixel i),
       // in shared memory when staged
+      // A chunk whose masks are sparse on every lane of the warp goes through
+      // its set bits only, its gradients staged in s_g[e][thread]
+      // (conflict-free); otherwise the unrolled form takes all 16 filters.
       float *dst = (staged ? stage : packed + seg_base[qa]) + po;
+      float *const gs = s_g + tid;
       for (int c = 0; c < NC; ++c) {
-        const uint32_t m = staged_mask(s_mw, c);
+        uint32_t m = staged_mask(s_mw, c);
         float g[16];
         tc::tmem_ld16(lane_addr + 16 * c, g);
+        if (__any_sync(0xffffffffu, __popc(m) > 6)) {
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          if ((m >> e) & 1u) {
-            *dst = soft_threshold(*dst - alpha * g[e], thr);
+          for (int e = 0; e < 16; ++e) {
+            if ((m >> e) & 1u) {
+              *dst = soft_threshold(*dst - alpha * g[e], thr);
+              ++dst;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) gs[e * kThreads] = g[e];
+          while (m != 0u) {
+            const int e = __ffs(m) - 1;
+            m &= m - 1u;
+            *dst = soft_threshold(*dst - alpha * gs[e * kThreads], thr);
             ++dst;
           }
         }
