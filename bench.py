@@ -392,6 +392,30 @@ def dict_report(steps=5):
     print(json.dumps(out), flush=True)
 
 
+def online_profile_step():
+    """One tensor code step of the online workload's first mini-batch (50 x
+    100x100 images, K = 400 11x11, p = 1/10, 4 PG iterations), every kernel
+    launched directly (no graph, no variant timing): a small case for ncu
+    captures of the single-stage kernels."""
+    import torch
+    from paper_1909_00145_gb300 import inputs as I
+    from paper_1909_00145_gb300 import scsc
+    K, s, eta, side = 400, 11, 50, 100
+    stream = torch.cuda.Stream()
+    H = np.full(eta, side, dtype=np.int32)
+    W = np.full(eta, side, dtype=np.int32)
+    d = torch.from_numpy(I.filters(7, K, s)).cuda().contiguous()
+    ctx = scsc.Context(K, s, 1.0, (1, 10), seed=0, prec="bf16", stream=stream,
+                       flags=scsc.SCSC_FLAG_NO_GRAPH | scsc.SCSC_FLAG_NO_AUTOTUNE)
+    with torch.cuda.stream(stream):
+        batch = scsc.Batch(H, W, np.arange(eta))
+        x = torch.from_numpy(I.images(5001, H, W)).cuda()
+        z = torch.zeros(eta * side * side * K, device="cuda")
+        ctx.code_step(batch, x, d, z, 1, 4)
+        stream.synchronize()
+    print(json.dumps({"online_profile_step": "ok", "l1": float(z.abs().sum())}), flush=True)
+
+
 def online_report(prec="bf16", batches=4):
     """The online workload of Alg. 2 at its stated size, on a prefix of the
     stream: mini-batches of eta = 50 new 100x100 images, K = 400 filters of
@@ -473,7 +497,12 @@ def main():
                     help="time the Jacobi and Gauss-Seidel dictionary steps and exit")
     ap.add_argument("--online", action="store_true",
                     help="time the online workload at K=400 (Alg. 2 prefix) and exit")
+    ap.add_argument("--online-profile", action="store_true",
+                    help="run one K=400 tensor code step (small case for ncu captures) and exit")
     args = ap.parse_args()
+    if args.online_profile:
+        online_profile_step()
+        return
     if args.online:
         online_report(args.prec)
         return

@@ -55,9 +55,10 @@ typedef enum {
 typedef enum {
   SCSC_FP32 = 0, /* plain path: FP32 SIMT kernels on dense FP32 codes          */
   SCSC_BF16 = 1, /* tensor path: BF16 operands on tcgen05, FP32 accumulation,
-                    FP32 residual / prox / projection; the sampled codes are
-                    stored in BF16 between iterations by the fused kernel
-                    (K <= 112 at s = 11), in FP32 by the two-kernel path       */
+                    FP32 residual / prox / projection, every K <= 512; the
+                    sampled codes are stored in BF16 between iterations by
+                    the fused kernel (K <= 112 at s = 11), in FP32 by the
+                    two-kernel and single-stage kernels                       */
   SCSC_TF32 = 2  /* TF32 operands: not built; scsc_create returns
                     SCSC_EUNSUPPORTED (the BF16 path meets the objective bound
                     and SCSC_FP32 is the full-precision path)                  */
