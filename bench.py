@@ -255,7 +255,7 @@ def cpu_baseline(wl, budget_s=20.0):
             if wl.get("solver") == "screen" else f"{iters} PG iterations")
     return {"value": pf / el / 1e9, "unit": "Gpix*filter/s", "cores": cores, "kind": "oracle",
             "sample": f"1 image {int(H[0])}x{int(W[0])} of the workload, K={wl['K']}, "
-                      f"{what} (FP64, dense adjoint, OpenMP), {el:.1f} s"}
+                      f"{what} (FP64, adjoint at the sampled coordinates, OpenMP), {el:.1f} s"}
 
 
 def run_reference(args, wl):

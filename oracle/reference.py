@@ -115,6 +115,15 @@ def adjoint(d, r, K: int, s: int, H: int, W: int) -> np.ndarray:
     return out
 
 
+def adjoint_sampled(d, r, mask, K: int, s: int, H: int, W: int, fill=np.nan) -> np.ndarray:
+    """The adjoint at the sampled coordinates; `fill` elsewhere."""
+    d, r = _f64(d), _f64(r)
+    m = np.ascontiguousarray(mask, dtype=np.uint8)
+    out = np.full(H * W * K, fill)
+    lib().orc_adjoint_sampled(K, s, H, W, _p(d), _p(r), _p(m), _p(out))
+    return out
+
+
 def filter_gradient(r, z, K: int, s: int, H: int, W: int) -> np.ndarray:
     r, z = _f64(r), _f64(z)
     out = np.empty(K * s * s)

@@ -100,6 +100,28 @@ void orc_adjoint(int K, int s, int H, int W, const double *d, const double *r,
       }
 }
 
+/* The same correlation at the sampled coordinates only (mask[(a W + b) K + k]
+ * set): the gradient of Eq. 3 with respect to its pDK sampled variables
+ * (Sec. 3.1).  Each value is the same sum, in the same order, as orc_adjoint's;
+ * entries off the sampled set are not written. */
+void orc_adjoint_sampled(int K, int s, int H, int W, const double *d, const double *r,
+                         const uint8_t *mask, double *g) {
+  const int c = (s - 1) / 2;
+#pragma omp parallel for schedule(static)
+  for (int a = 0; a < H; ++a)
+    for (int b = 0; b < W; ++b)
+      for (int k = 0; k < K; ++k) {
+        const size_t i = ((size_t)a * W + b) * K + k;
+        if (!mask[i]) continue;
+        double acc = 0.0;
+        for (int u = 0; u < s; ++u)
+          for (int v = 0; v < s; ++v)
+            acc += d[((size_t)k * s + u) * s + v] *
+                   pix_at(r, H, W, a - c + u, b - c + v);
+        g[i] = acc;
+      }
+}
+
 /* G_k(u,v) = sum_{i,j} r(i,j) z_k(i+c-u, j+c-v) = (Z^T r)_{k,u,v}. */
 void orc_filter_gradient(int K, int s, int H, int W, const double *r,
                          const double *z, double *G) {
@@ -168,7 +190,7 @@ void orc_code_update_image(int K, int s, int H, int W, const double *d,
   for (int it = 0; it < n_iters; ++it) {
     orc_synthesis(K, s, H, W, d, z, r);
     for (size_t i = 0; i < D; ++i) r[i] -= x[i];
-    orc_adjoint(K, s, H, W, d, r, g);
+    orc_adjoint_sampled(K, s, H, W, d, r, mask, g);
     for (size_t i = 0; i < DK; ++i)
       if (mask[i]) z[i] = orc_soft_threshold(z[i] - alpha * g[i], alpha * lambda);
   }
@@ -191,7 +213,7 @@ void orc_code_update_image_keep(int K, int s, int H, int W, const double *d,
   for (int it = 0; it < n_iters; ++it) {
     orc_synthesis(K, s, H, W, d, z, r);
     for (size_t i = 0; i < D; ++i) r[i] -= x[i];
-    orc_adjoint(K, s, H, W, d, r, g);
+    orc_adjoint_sampled(K, s, H, W, d, r, mask, g);
     for (size_t i = 0; i < DK; ++i)
       if (mask[i]) z[i] = orc_soft_threshold(z[i] - alpha * g[i], alpha * lambda);
   }
@@ -230,7 +252,7 @@ void orc_code_update_image_observed(int K, int s, int H, int W, const double *d,
     orc_synthesis(K, s, H, W, d, z, r);
     /* gradient of 0.5 || O (x - D z) ||^2 is D^T O (D z - x) */
     for (size_t i = 0; i < D; ++i) r[i] = obs[i] ? r[i] - x[i] : 0.0;
-    orc_adjoint(K, s, H, W, d, r, g);
+    orc_adjoint_sampled(K, s, H, W, d, r, mask, g);
     for (size_t i = 0; i < DK; ++i)
       if (mask[i]) z[i] = orc_soft_threshold(z[i] - alpha * g[i], alpha * lambda);
   }

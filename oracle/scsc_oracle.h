@@ -46,6 +46,10 @@ void orc_synthesis(int K, int s, int H, int W, const double *d, const double *z,
 /* Adjoint D^T r: (D^T r)_k(a,b) = sum_{u,v} d_k(u,v) r(a-c+u, b-c+v). */
 void orc_adjoint(int K, int s, int H, int W, const double *d, const double *r,
                  double *g);
+/* The adjoint at the sampled coordinates only (mask[(a W + b) K + k] set), the
+ * gradient of Eq. 3 in its pDK variables; other entries of g are not written. */
+void orc_adjoint_sampled(int K, int s, int H, int W, const double *d, const double *r,
+                         const uint8_t *mask, double *g);
 
 /* Filter gradient Z^T r: G_k(u,v) = sum_{i,j} r(i,j) z_k(i+c-u, j+c-v)
  * (gradient of Eq. 5's data term).  Writes G [K][s][s]. */

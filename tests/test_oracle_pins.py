@@ -168,6 +168,24 @@ def test_adjoint_identities(K, s, H, W):
     assert abs(lhs - np.dot(d, R.filter_gradient(r, z, K, s, H, W))) <= 1e-13 * max(1.0, abs(lhs))
 
 
+@pytest.mark.parametrize("K,s,H,W,p", [(3, 5, 13, 17, 0.25), (5, 11, 20, 16, 0.1),
+                                       (4, 3, 2, 9, 1.0), (2, 7, 6, 5, 0.0)])
+def test_adjoint_at_sampled_coordinates(K, s, H, W, p):
+    """The gradient of Eq. 3 in its sampled variables: the explicit matrix's
+    rows A^T r at the sampled coordinates, bit for bit the dense adjoint's
+    values there, and nothing written elsewhere."""
+    d = rng(11).normal(size=K * s * s)
+    r = rng(12).normal(size=H * W)
+    mask = (rng(13).random(H * W * K) < p).astype(np.uint8)
+    g = R.adjoint_sampled(d, r, mask, K, s, H, W)
+    on = mask.astype(bool)
+    assert np.array_equal(g[on], R.adjoint(d, r, K, s, H, W)[on])
+    assert np.all(np.isnan(g[~on]))
+    if H * W <= 64:
+        A = explicit_synthesis_matrix(d.reshape(K, s, s), H, W)
+        np.testing.assert_allclose(g[on], (A.T @ r)[on], atol=1e-13)
+
+
 def test_brute_force_8x8_operators_and_lipschitz():
     K, s, H, W = 2, 5, 8, 8
     d = I.filters(1, K, s).astype(np.float64)
