@@ -4,8 +4,13 @@
 // Z_n is the code Toeplitz matrix of image n: row (i,j), column (k,u,v),
 // entry z_k(i+c-u, j+c-v).  The surrogate update
 //     C <- a C + b sum_n Z_n^T Z_n,     B <- a B + b sum_n Z_n^T x_n
-// is an implicit GEMM over all pixels of the batch: Z is never materialised,
-// its entries are gathered from the codes while staging tiles in shared memory.
+// has two forms.  For dense codes it is an implicit GEMM over all pixels of
+// the batch: Z is never materialised, its entries are gathered from the codes
+// while staging tiles in shared memory.  For codes sparser than 1/16 it is
+// built from the nonzero codes: cross-correlations of the code maps at the
+// lag between two columns, expanded into C's upper block triangle, minus the
+// products of patches centred outside the image, then mirrored.  The
+// products with C read its upper block triangle only.
 #include <algorithm>
 
 #include "scsc_internal.cuh"

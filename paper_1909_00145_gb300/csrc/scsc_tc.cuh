@@ -122,7 +122,10 @@ struct CorrSegments {
 };
 void surrogate_corr_segments(int K, int s, int64_t nnz, int *seg_len, int64_t *max_segments);
 // The same update from the index of the nonzero codes (dictionary-step index
-// of kernels_sparse.cu), O(nnz * patch nonzeros) instead of O(D (K s^2)^2).
+// of kernels_sparse.cu): with T (surrogate_corr_floats(K, s) floats) and segs,
+// the correlation form, O(nnz * (2s-1)^2 * nonzeros per pixel) plus the
+// border patches; with T == nullptr the per-patch walk, O(nnz * patch
+// nonzeros) per row of C.
 cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, const float *x,
                                            const int64_t *row_ptr, const int *pk, const float *pv,
                                            const int64_t *kt_off, const int *kpix,
