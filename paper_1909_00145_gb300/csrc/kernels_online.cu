@@ -222,71 +222,6 @@ __global__ void __launch_bounds__(256) symv_reduce_kernel(const float *__restric
   }
 }
 
-// The same update from the index of the nonzero codes (kernels_sparse.cu):
-// one warp per row a = (k, u, v) of C, over the columns of filters k2 >= k
-// only (C is symmetric; mirror_lower_kernel copies the rest).  Row a of Z^T Z collects, for every
-// nonzero z_k(q1), the pixel q = q1 - c + (u, v) whose patch holds it in
-// column a, times every nonzero of q's patch: z_k2(q2) with q2 in the s x s
-// window of q lands in column (k2, u2, v2), (u2, v2) = q + c - q2.  The row
-// is decayed first; the lanes then split each patch's window, whose nonzeros
-// fall in distinct columns, and a warp barrier orders one patch's updates
-// before the next's, so the sums are deterministic.  B[a] accumulates
-// z_k(q1) x(q) in FP64 on lane 0.
-__global__ void __launch_bounds__(256) surrogate_sparse_kernel(
-    BatchDev b, int K, int S, const float *__restrict__ x, const int64_t *__restrict__ row_ptr,
-    const int *__restrict__ pk, const float *__restrict__ pv, const int64_t *__restrict__ kt_off,
-    int ntiles, const int *__restrict__ kpix, const int *__restrict__ kimg,
-    const float *__restrict__ kv, int KM, float alpha, float beta, float *__restrict__ Cm,
-    double *__restrict__ Bv) {
-  const int64_t a = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x & 31;
-  if (a >= KM) return;
-  const int M = S * S, C = (S - 1) / 2;
-  const int k = (int)(a / M), m = (int)(a - (int64_t)k * M), u = m / S, v = m - (m / S) * S;
-  float *const crow = Cm + a * KM;
-  if (alpha != 1.0f)
-    for (int64_t j = (int64_t)k * M + lane; j < KM; j += 32) crow[j] *= alpha;
-  __syncwarp();
-  double bsum = 0.0;
-  const int64_t kb = kt_off[(int64_t)k * ntiles], ke = kt_off[(int64_t)(k + 1) * ntiles];
-  for (int64_t e = kb; e < ke; ++e) {
-    const int n = kimg[e];
-    const int H = b.H[n], W = b.W[n];
-    const int64_t base = b.off[n];
-    const int local = (int)(kpix[e] - base);
-    const int y = local / W - C + u, xx = local - (local / W) * W - C + v;
-    if (y < 0 || y >= H || xx < 0 || xx >= W) continue;  // the same on every lane
-    const float z1 = kv[e];
-    if (lane == 0) bsum += (double)z1 * (double)x[base + (int64_t)y * W + xx];
-    // the window's offsets first (up to 4 pixels per lane, s <= 11), so that
-    // their loads are in flight together
-    int64_t rb[4], re[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int wi = lane + 32 * r;
-      rb[r] = re[r] = 0;
-      if (wi < M) {
-        const int u2 = wi / S, v2 = wi - (wi / S) * S;
-        const int y2 = y + C - u2, x2 = xx + C - v2;
-        if (y2 >= 0 && y2 < H && x2 >= 0 && x2 < W) {
-          const int64_t g2 = base + (int64_t)y2 * W + x2;
-          rb[r] = row_ptr[g2];
-          re[r] = row_ptr[g2 + 1];
-        }
-      }
-    }
-    const float bz = beta * z1;
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-      for (int64_t e2 = rb[r]; e2 < re[r]; ++e2) {
-        const int k2 = pk[e2];
-        if (k2 >= k) crow[(int64_t)k2 * M + lane + 32 * r] += bz * pv[e2];
-      }
-    __syncwarp();
-  }
-  if (lane == 0) Bv[a] = (double)alpha * Bv[a] + (double)beta * bsum;
-}
-
 // Cross-correlations of the code maps for the surrogate update:
 //   T[k][k2][dy][dx] = sum over nonzeros z_k(r1) with r1 + (dy, dx) in the
 //   same image of z_k(r1) z_k2(r1 + (dy, dx)),  k2 >= k, |dy|, |dx| <= s - 1.
@@ -534,32 +469,26 @@ cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, cons
   const int KM = K * s * s;
   const int nt_px = sparse_tiles(b.total_px);
   cudaError_t e;
-  if (T != nullptr) {
-    // correlations, then C = alpha C + beta T (upper blocks), then the
-    // border corrections and B
-    if (segs == nullptr || segs->max_segments > 0x7fffffff) return cudaErrorInvalidValue;
-    corr_segments_kernel<<<1, 32, 0, st>>>(kt_off, nt_px, K, segs->seg_len, segs->seg_off);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    surrogate_corr_kernel<<<(unsigned)segs->max_segments, 512, 0, st>>>(
-        b, K, s, row_ptr, pk, pv, kt_off, nt_px, kpix, kimg, kv, segs->seg_off, segs->seg_len,
-        segs->P, T);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int DD = (2 * s - 1) * (2 * s - 1);
-    corr_reduce_kernel<<<dim3((unsigned)(((int64_t)K * DD + 255) / 256), K), 256, 0, st>>>(
-        segs->P, segs->seg_off, K, DD, T);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    surrogate_expand_kernel<<<KM, 256, 0, st>>>(Cm, T, K, s, (float)alpha, (float)beta);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const int64_t blocks = ((int64_t)KM + 7) / 8;
-    surrogate_border_kernel<<<(unsigned)blocks, 256, 0, st>>>(
-        b, K, s, x, row_ptr, pk, pv, kt_off, nt_px, kpix, kimg, kv, KM, (float)alpha,
-        (float)beta, Cm, Bv);
-  } else {
-    const int64_t blocks = ((int64_t)KM + 7) / 8;
-    surrogate_sparse_kernel<<<(unsigned)blocks, 256, 0, st>>>(
-        b, K, s, x, row_ptr, pk, pv, kt_off, nt_px, kpix, kimg, kv, KM, (float)alpha,
-        (float)beta, Cm, Bv);
-  }
+  if (T == nullptr || segs == nullptr || segs->max_segments > 0x7fffffff)
+    return cudaErrorInvalidValue;
+  // correlations, then C = alpha C + beta T (upper blocks), then the border
+  // corrections and B, then the lower blocks
+  corr_segments_kernel<<<1, 32, 0, st>>>(kt_off, nt_px, K, segs->seg_len, segs->seg_off);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  surrogate_corr_kernel<<<(unsigned)segs->max_segments, 512, 0, st>>>(
+      b, K, s, row_ptr, pk, pv, kt_off, nt_px, kpix, kimg, kv, segs->seg_off, segs->seg_len,
+      segs->P, T);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int DD = (2 * s - 1) * (2 * s - 1);
+  corr_reduce_kernel<<<dim3((unsigned)(((int64_t)K * DD + 255) / 256), K), 256, 0, st>>>(
+      segs->P, segs->seg_off, K, DD, T);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  surrogate_expand_kernel<<<KM, 256, 0, st>>>(Cm, T, K, s, (float)alpha, (float)beta);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int64_t blocks = ((int64_t)KM + 7) / 8;
+  surrogate_border_kernel<<<(unsigned)blocks, 256, 0, st>>>(
+      b, K, s, x, row_ptr, pk, pv, kt_off, nt_px, kpix, kimg, kv, KM, (float)alpha,
+      (float)beta, Cm, Bv);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nt = (KM + 31) / 32;

@@ -122,18 +122,16 @@ struct CorrSegments {
 };
 void surrogate_corr_segments(int K, int s, int64_t nnz, int *seg_len, int64_t *max_segments);
 // The same update from the index of the nonzero codes (dictionary-step index
-// of kernels_sparse.cu): with T (surrogate_corr_floats(K, s) floats) and segs,
-// the correlation form, O(nnz * (2s-1)^2 * nonzeros per pixel) plus the
-// border patches; with T == nullptr the per-patch walk, O(nnz * patch
-// nonzeros) per row of C.
+// of kernels_sparse.cu) in the correlation form: O(nnz * (2s-1)^2 * nonzeros
+// per pixel) plus the patches centred outside the image.  T holds
+// surrogate_corr_floats(K, s) floats.
 cudaError_t launch_surrogate_update_sparse(const BatchDev &b, int K, int s, const float *x,
                                            const int64_t *row_ptr, const int *pk, const float *pv,
                                            const int64_t *kt_off, const int *kpix,
                                            const int *kimg, const float *kv, double alpha,
                                            double beta, float *Cm, double *Bv, float *T,
                                            const CorrSegments *segs, cudaStream_t st);
-// Floats of the correlation buffer T of that update (K * K * (2s-1)^2); with
-// T == nullptr the update walks every patch instead (no buffer).
+// Floats of the correlation buffer T of that update (K * K * (2s-1)^2).
 size_t surrogate_corr_floats(int K, int s);
 // out = C v (FP32 out) and out = C d - B (FP64 out) for the symmetric C of
 // order n, from its upper block triangle; part holds symv_panels(n) * n
